@@ -1,0 +1,365 @@
+"""Pins for the CPU oracle: each test ties it to something other than itself --
+the paper's worked example, dense or brute-force arithmetic, library routines,
+algebraic identities and closed forms.  No GPU is needed."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def to_dense(C, m=None):
+    m = C["nrows"] if m is None else m
+    n = C["ncols"]
+    D = np.zeros((m, n), dtype=C["vals"].dtype)
+    for j in range(n):
+        s, e = C["colptr"][j], C["colptr"][j + 1]
+        D[C["rowidx"][s:e], j] = C["vals"][s:e]
+    return D
+
+
+def pattern_dense(C):
+    P = np.zeros((C["nrows"], C["ncols"]), dtype=bool)
+    for j in range(C["ncols"]):
+        s, e = C["colptr"][j], C["colptr"][j + 1]
+        P[C["rowidx"][s:e], j] = True
+    return P
+
+
+def to_scipy(M):
+    return sp.csc_matrix((np.asarray(M.vals), np.asarray(M.rowidx, dtype=np.int64),
+                          np.asarray(M.colptr, dtype=np.int64)), shape=(M.nrows, M.ncols))
+
+
+def from_scipy(S, idx=np.int32):
+    S = sp.csc_matrix(S)
+    S.sort_indices()
+    return synth.CSC(S.shape[0], S.shape[1], S.indptr.astype(np.int64), S.indices.astype(idx), S.data.copy())
+
+
+def result_as_csc(C):
+    return synth.CSC(C["nrows"], C["ncols"], C["colptr"], C["rowidx"], C["vals"])
+
+
+def assert_sorted_unique(C):
+    for j in range(C["ncols"]):
+        r = C["rowidx"][C["colptr"][j]:C["colptr"][j + 1]]
+        assert np.all(np.diff(r) > 0), f"column {j} rows not strictly increasing"
+
+
+# ---------------------------------------------------------------- paper example
+
+def test_fig1_H0_and_block_fetch():
+    """Fig. 1 / Section 3.1: H_0 = [1,0,1,1,0,1,0,0]; with 2 blocks of 2 column
+    ids per owner, p_0 fetches blocks (0,0), (0,1) and (1,0) but not (1,1)."""
+    g = json.load(open(os.path.join(GOLD, "fig1_h0.json")))
+    A, B = synth.fig1_example()
+    pl = oracle.plan_block(A, B, 0, 4, g["b"])
+    assert pl["H"].tolist() == g["H0"]
+    assert pl["dtilde"].tolist() == g["required_columns_p0"]
+    assert pl["fetch"].tolist() == g["fetch_blocks_p0"]
+    assert pl["intervals"].tolist() == g["fetched_intervals_p0"]
+    # chosen blocks are read whole: columns 1 and 4 come along unused
+    unused = int(A.colptr[2] - A.colptr[1]) + int(A.colptr[5] - A.colptr[4])
+    assert pl["vol_block"] == pl["vol_exact"] + unused
+    # the whole of Algorithm 1 reproduces the plain product on this example
+    C1, _ = oracle.spgemm_1d(A, B, P=2, b=2)
+    C = oracle.spgemm(A, B)
+    assert np.array_equal(C1["colptr"], C["colptr"]) and np.array_equal(C1["rowidx"], C["rowidx"])
+    assert np.array_equal(C1["vals"], C["vals"])
+
+
+# ------------------------------------------------------------ dense arithmetic
+
+@pytest.mark.parametrize("seed", range(6))
+def test_dense_matmul_small_integers(seed):
+    """Small-integer values make every double sum exact, so the oracle must equal
+    numpy's dense product bit for bit; its pattern must equal the boolean
+    product of the patterns (no cancellation is dropped)."""
+    rng = np.random.default_rng(seed)
+    m, k, n = rng.integers(1, 40, size=3)
+    A = synth.random_sparse(m, k, 0.25, rng, values="small")
+    B = synth.random_sparse(k, n, 0.25, rng, values="small")
+    C = oracle.spgemm(A, B)
+    assert_sorted_unique(C)
+    Ad, Bd = to_dense_csc(A), to_dense_csc(B)
+    assert np.array_equal(to_dense(C), Ad @ Bd)
+    patt = ((Ad != 0).astype(np.int64) @ (Bd != 0).astype(np.int64)) > 0
+    assert np.array_equal(pattern_dense(C), patt)
+    # integer semiring on the same data
+    Ci = oracle.spgemm(A.astype(val=np.int64), B.astype(val=np.int64))
+    assert np.array_equal(Ci["colptr"], C["colptr"]) and np.array_equal(Ci["rowidx"], C["rowidx"])
+    assert np.array_equal(to_dense(Ci), (Ad @ Bd).astype(np.int64))
+
+
+def to_dense_csc(M):
+    D = np.zeros((M.nrows, M.ncols), dtype=np.asarray(M.vals).dtype)
+    for j in range(M.ncols):
+        r, v = M.col(j)
+        D[r, j] = v
+    return D
+
+
+def test_brute_force_triple_loop_with_cancellation():
+    """Brute force over (r, k, j) on tiny inputs, including explicit zeros and
+    sums that cancel: every position with at least one product is present."""
+    rng = np.random.default_rng(11)
+    for trial in range(25):
+        m, k, n = rng.integers(1, 7, size=3)
+        A = synth.random_sparse(m, k, 0.5, rng, values="small")
+        B = synth.random_sparse(k, n, 0.5, rng, values="small")
+        A.vals[rng.random(A.nnz) < 0.2] = 0.0        # stored zeros stay structural
+        Ad, Bd = to_dense_csc(A), to_dense_csc(B)
+        Am = np.zeros((m, k), bool)
+        Bm = np.zeros((k, n), bool)
+        for j in range(k):
+            Am[A.col(j)[0], j] = True
+        for j in range(n):
+            Bm[B.col(j)[0], j] = True
+        C = oracle.spgemm(A, B)
+        for j in range(n):
+            want_rows, want_vals = [], []
+            for r in range(m):
+                terms = [Ad[r, kk] * Bd[kk, j] for kk in range(k) if Am[r, kk] and Bm[kk, j]]
+                if terms:
+                    want_rows.append(r)
+                    want_vals.append(sum(terms))
+            s, e = C["colptr"][j], C["colptr"][j + 1]
+            assert C["rowidx"][s:e].tolist() == want_rows
+            assert C["vals"][s:e].tolist() == want_vals
+    # an explicit cancelling case: [1 1] * [1; -1] = 0, still one stored entry
+    A = synth.CSC(1, 2, np.array([0, 1, 2]), np.array([0, 0], np.int32), np.array([1.0, 1.0]))
+    B = synth.CSC(2, 1, np.array([0, 2]), np.array([0, 1], np.int32), np.array([1.0, -1.0]))
+    C = oracle.spgemm(A, B)
+    assert C["colptr"].tolist() == [0, 1] and C["vals"].tolist() == [0.0] and C["absum"].tolist() == [2.0]
+
+
+def test_int64_semiring_wraps_modulo_2_64():
+    """The integer semiring is exact arithmetic modulo 2^64 (Python big ints)."""
+    rng = np.random.default_rng(5)
+    for trial in range(10):
+        m, k, n = rng.integers(1, 6, size=3)
+        A = synth.random_sparse(m, k, 0.6, rng, values="i64big")
+        B = synth.random_sparse(k, n, 0.6, rng, values="i64big")
+        C = oracle.spgemm(A, B)
+        Ad = [[0] * k for _ in range(m)]
+        Bd = [[0] * n for _ in range(k)]
+        for j in range(k):
+            for r, v in zip(*A.col(j)):
+                Ad[r][j] = int(v)
+        for j in range(n):
+            for r, v in zip(*B.col(j)):
+                Bd[r][j] = int(v)
+        got = to_dense(C)
+        for r in range(m):
+            for j in range(n):
+                s = sum(Ad[r][kk] * Bd[kk][j] for kk in range(k)) % (1 << 64)
+                if s >= 1 << 63:
+                    s -= 1 << 64
+                assert int(got[r, j]) == s
+
+
+# ------------------------------------------------------------------ identities
+
+@pytest.mark.parametrize("seed", range(4))
+def test_transpose_identity(seed):
+    """(AB)^T = B^T A^T, the transposes taken by scipy; same terms in the same
+    k order, so equal bit for bit."""
+    rng = np.random.default_rng(100 + seed)
+    A = synth.random_sparse(50, 37, 0.08, rng)
+    B = synth.random_sparse(37, 61, 0.08, rng)
+    C = oracle.spgemm(A, B)
+    At, Bt = from_scipy(to_scipy(A).T), from_scipy(to_scipy(B).T)
+    Ct = oracle.spgemm(Bt, At)
+    lhs = sp.csc_matrix(to_scipy(result_as_csc(C)).T)
+    lhs.sort_indices()
+    assert np.array_equal(lhs.indptr, Ct["colptr"]) and np.array_equal(lhs.indices, Ct["rowidx"])
+    assert np.array_equal(lhs.data, Ct["vals"])
+
+
+def test_identity_is_neutral():
+    """A*I = A and I*A = A."""
+    rng = np.random.default_rng(3)
+    A = synth.random_sparse(40, 30, 0.1, rng)
+    I30 = synth.CSC(30, 30, np.arange(31), np.arange(30, dtype=np.int32), np.ones(30))
+    I40 = synth.CSC(40, 40, np.arange(41), np.arange(40, dtype=np.int32), np.ones(40))
+    for C in (oracle.spgemm(A, I30), oracle.spgemm(I40, A)):
+        assert np.array_equal(C["colptr"], A.colptr)
+        assert np.array_equal(C["rowidx"], A.rowidx)
+        assert np.array_equal(C["vals"], A.vals)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 7])
+@pytest.mark.parametrize("b", [1, 2, 5, 32, 1000])
+def test_union_of_blocks_equals_unpartitioned(P, b):
+    """Algorithm 1 on P blocks (gather A~_i, multiply A~_i * B_i, concatenate)
+    gives exactly the plain product: the partition and the fetch blocks only
+    choose which data is touched (Section 3.1)."""
+    rng = np.random.default_rng(P * 1000 + b)
+    A = synth.random_sparse(45, 40, 0.07, rng)
+    B = synth.random_sparse(40, 33, 0.07, rng)
+    C = oracle.spgemm(A, B)
+    C1, plans = oracle.spgemm_1d(A, B, P, b)
+    for key in ("colptr", "rowidx", "vals", "absum"):
+        assert np.array_equal(C1[key], C[key]), key
+    assert len(plans) == P
+
+
+def test_flop_identity_and_nnz_bound():
+    """Section 3.2: the number of products is the inner product of the column
+    counts of A with the row counts of B, and nnz(C) <= products."""
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        A = synth.random_sparse(60, 50, 0.1, rng)
+        B = synth.random_sparse(50, 70, 0.1, rng)
+        C = oracle.spgemm(A, B)
+        colnnz_A = np.diff(A.colptr)
+        rownnz_B = np.bincount(B.rowidx, minlength=B.nrows)
+        products = int(colnnz_A @ rownnz_B)
+        assert int(C["flops"].sum()) == products
+        assert int(C["colptr"][-1]) <= products
+        f = oracle.features(A, B)
+        assert np.array_equal(f["flops"], C["flops"])
+        assert np.array_equal(f["nnzb"], np.diff(B.colptr))
+
+
+def test_pattern_matches_scipy_all_ones_product():
+    """With all-ones values nothing cancels, so the oracle's pattern equals the
+    pattern of scipy's product (a library routine)."""
+    rng = np.random.default_rng(21)
+    A = synth.random_sparse(300, 200, 0.02, rng, values="ones")
+    B = synth.random_sparse(200, 250, 0.02, rng, values="ones")
+    C = oracle.spgemm(A, B)
+    S = sp.csc_matrix(to_scipy(A) @ to_scipy(B))
+    S.sort_indices()
+    assert np.array_equal(S.indptr, C["colptr"]) and np.array_equal(S.indices, C["rowidx"])
+    assert np.array_equal(S.data, C["vals"])
+
+
+# ------------------------------------------------------------- Algorithm 2
+
+@pytest.mark.parametrize("seed", range(5))
+def test_block_fetch_contract(seed):
+    """Algorithm 2: the chosen intervals cover every required column, M <= K,
+    every chosen block holds a required column, and the volumes are ordered
+    exact <= block-granular <= nnz(A)."""
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(1, 300))
+    A = synth.random_sparse(80, k, 0.03, rng)
+    B = synth.random_sparse(k, 90, 0.01, rng)
+    for b in (1, 3, 32, 64, 1000):
+        for c0, c1 in ((0, 90), (10, 40), (50, 50)):
+            pl = oracle.plan_block(A, B, c0, c1, b)
+            H = np.zeros(k, np.uint8)
+            for j in range(c0, c1):
+                H[B.col(j)[0]] = 1
+            assert np.array_equal(pl["H"], H)
+            nonempty = np.diff(A.colptr) > 0
+            assert pl["dtilde"].tolist() == np.flatnonzero(H.astype(bool) & nonempty).tolist()
+            K = (k + b - 1) // b
+            assert pl["fetch"].shape[0] == K and pl["fetch"].sum() <= K
+            for h in pl["dtilde"]:
+                assert any(lo <= h <= hi for lo, hi in pl["intervals"])
+            for lo, hi in pl["intervals"]:
+                assert np.any((pl["dtilde"] >= lo) & (pl["dtilde"] <= hi))
+            assert pl["vol_exact"] <= pl["vol_block"] <= A.nnz
+            At = oracle.gather(A, pl["dtilde"])
+            assert int(At["colptr"][-1]) == pl["vol_exact"]
+
+
+# ------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_galerkin_closed_form(N):
+    """7-point Laplacian (diag 6, off-diagonal -1) and 2x2x2 aggregation with
+    entries 1/sqrt(8).  Row v of A*P_agg: 3/sqrt(8) on its own aggregate (6 minus
+    its 3 neighbours inside the aggregate) and -1/sqrt(8) on each aggregate
+    reached through an outer face; nnz(A*P_agg) = 4N^3 - 6N^2.  The coarse
+    operator P^T A P is the (N/2)^3 7-point operator with diagonal 3 and face
+    off-diagonals -1/2, nnz = 7M^3 - 6M^2 with M = N/2."""
+    A = synth.poisson3d(N)
+    Pg = synth.aggregation_2x2x2(N)
+    PT = synth.aggregation_2x2x2_transpose(N)
+    AP = oracle.spgemm(A, Pg)
+    assert int(AP["colptr"][-1]) == 4 * N ** 3 - 6 * N ** 2
+    s8 = 1.0 / math.sqrt(8.0)
+    M = N // 2
+    D = to_dense(AP)
+    for v in range(N ** 3):
+        x, y, z = v // (N * N), (v // N) % N, v % N
+        want = {((x // 2) * M + y // 2) * M + z // 2: 3 * s8}
+        for axis, c in ((0, x), (1, y), (2, z)):
+            step = -1 if c % 2 == 0 else 1          # the outer neighbour along this axis
+            cc = c + step
+            if 0 <= cc < N:
+                xyz = [x, y, z]
+                xyz[axis] = cc
+                want[((xyz[0] // 2) * M + xyz[1] // 2) * M + xyz[2] // 2] = -s8
+        nz = np.flatnonzero(D[v] != 0)
+        assert sorted(want) == nz.tolist()
+        for J, val in want.items():
+            assert abs(D[v, J] - val) <= 1e-15
+    APc = result_as_csc(AP)
+    G = oracle.spgemm(PT, APc)
+    assert int(G["colptr"][-1]) == 7 * M ** 3 - 6 * M ** 2
+    Gd = to_dense(G)
+    for I in range(M ** 3):
+        X, Y, Z = I // (M * M), (I // M) % M, I % M
+        for J in range(M ** 3):
+            X2, Y2, Z2 = J // (M * M), (J // M) % M, J % M
+            dist = abs(X - X2) + abs(Y - Y2) + abs(Z - Z2)
+            want = 3.0 if dist == 0 else (-0.5 if dist == 1 else 0.0)
+            assert abs(Gd[I, J] - want) <= 1e-12 * max(1.0, abs(want)) * 8
+
+
+def test_graph_squaring_properties():
+    """Squaring a symmetric 0/1 graph: C is symmetric, C_ii = deg(i), and the
+    double run (values 1.0) equals the int64 path-count run exactly."""
+    A = synth.rmat_symmetric(9, 8, seed=1)
+    Ai = synth.rmat_symmetric(9, 8, seed=1, values="i64")
+    C = oracle.spgemm(A, A)
+    Ci = oracle.spgemm(Ai, Ai)
+    assert np.array_equal(C["colptr"], Ci["colptr"]) and np.array_equal(C["rowidx"], Ci["rowidx"])
+    assert np.array_equal(C["vals"].astype(np.int64), Ci["vals"])
+    S = to_scipy(result_as_csc(C))
+    assert (S != S.T).nnz == 0
+    deg = np.diff(A.colptr)
+    assert np.array_equal(S.diagonal(), deg.astype(np.float64))
+
+
+def test_similarity_product_diagonal():
+    """C = A*A^T for an integer matrix: symmetric with C_ii = sum_k a_ik^2."""
+    A, At = synth.lognormal_zipf_rows(nrows=300, ncols=2000, mean=8, cap=40, seed=2)
+    C = oracle.spgemm(A.astype(val=np.int64), At.astype(val=np.int64))
+    S = to_scipy(result_as_csc(C))
+    assert (S != S.T).nnz == 0
+    sq = np.zeros(300, np.int64)
+    for j in range(At.ncols):
+        r, v = At.col(j)
+        sq[j] = int(np.sum(v.astype(np.int64) ** 2))
+    assert np.array_equal(S.diagonal(), sq)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_and_degenerate_shapes():
+    z = lambda m, n: synth.CSC(m, n, np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    for m, k, n in ((0, 0, 0), (3, 0, 4), (0, 5, 2), (4, 5, 0), (3, 4, 5)):
+        C = oracle.spgemm(z(m, k), z(k, n))
+        assert C["colptr"].tolist() == [0] * (n + 1)
+    rng = np.random.default_rng(0)
+    A = synth.random_sparse(1, 6, 0.5, rng)
+    B = synth.random_sparse(6, 1, 0.5, rng)
+    C = oracle.spgemm(A, B)
+    assert C["colptr"][-1] <= 1
+    with pytest.raises(ValueError):
+        oracle.spgemm(z(3, 4), z(5, 2))
+    C1, plans = oracle.spgemm_1d(z(3, 4), z(4, 5), P=3, b=2)
+    assert C1["colptr"].tolist() == [0] * 6 and all(p["dtilde"].size == 0 for p in plans)
