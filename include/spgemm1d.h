@@ -1,0 +1,192 @@
+/*
+ * spgemm1d.h -- C ABI of the GB300 sparsity-aware 1D SpGEMM, C = A * B.
+ *
+ * The operation (Section 2, problem statement; Section 3.1, Algorithm 1):
+ * A is m x k, B is k x n, C is m x n, all in compressed sparse column (CSC)
+ * form.  B and C are split into P column blocks; block i holds columns
+ * [floor(i*n/P), floor((i+1)*n/P)) (Algorithm 1 only asks that the n_i sum
+ * to n).  For every block the library
+ *   1. marks H_i, the nonzero rows of B_i (Table 1; Algorithm 1, step on H_i),
+ *   2. forms the required column ids D~_i = H_i AND D, D = nonempty columns of
+ *      A (Algorithm 1, step on D~), and chooses fetch blocks of b consecutive
+ *      column ids, a block being chosen iff it holds a required column
+ *      (Algorithm 2 with fixed-width groups),
+ *   3. gathers A~_i = A(:, D~_i), reading A one chosen fetch block per work
+ *      unit (Algorithm 1, one-sided fetch and "new sparse matrix" steps),
+ *   4. counts per output column the sparse flops (Section 3.2) and bins the
+ *      columns,
+ *   5. runs a symbolic pass giving nnz(C(:,j)) and the column pointers of C,
+ *   6. runs a numeric pass giving the sorted rows and values of C
+ *      (Algorithm 1, local multiply C_i = A~_i * B_i, Gustavson form).
+ *
+ * Result contract: a position (r, j) of C is present iff at least one product
+ * a_rk * b_kj exists (sums that cancel to zero stay stored); rows within a
+ * column strictly increase; integer values use the (+, x) semiring on 64-bit
+ * two's-complement words (wrapping); double values are sums in an unspecified
+ * order (each entry within 1e-12 * sum |a_rk * b_kj| of the exact sum).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrix arrays are DEVICE pointers owned by the caller.  Inputs must be
+ *     canonical: colptr[0] = 0, non-decreasing, colptr[ncols] = nnz, row ids
+ *     in [0, nrows) and strictly increasing within each column.  With
+ *     spg_options.validate = 1 (the default of spgemm_default_options) the
+ *     plan checks this and returns SPG_INVALID_INPUT otherwise.
+ *   - All work is ordered on spg_options.stream (a cudaStream_t; NULL is the
+ *     legacy default stream).  Only the calls documented as synchronising wait
+ *     on the host.
+ *   - Errors are returned as spg_status; spgemm_last_error() gives a message
+ *     for the calling thread.  No C++ exception crosses this boundary.
+ *   - A, B and C may not alias.  A plan keeps pointers to A and B: they must
+ *     stay valid and unchanged until spgemm_plan_destroy.
+ */
+#ifndef SPGEMM1D_H
+#define SPGEMM1D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPG_OK = 0,
+    SPG_INVALID_ARGUMENT = 1,   /* null pointer, bad enum, dimension mismatch (A.ncols != B.nrows) */
+    SPG_INVALID_INPUT = 2,      /* input not canonical: colptr not monotone, row out of range / unsorted / repeated */
+    SPG_OUT_OF_MEMORY = 3,      /* a workspace or output allocation failed */
+    SPG_CUDA_ERROR = 4,         /* a CUDA runtime call or kernel launch failed */
+    SPG_TIMEOUT = 5,            /* a bounded device-side wait gave up (batched executor) */
+    SPG_UNSUPPORTED = 6,        /* sizes beyond this build's limits (e.g. m >= 2^31) */
+    SPG_OVERFLOW_RECOMPUTED = 7 /* informational: learned sizing under-predicted some columns, they were recomputed exactly */
+} spg_status;
+
+typedef enum { SPG_IDX_I32 = 0, SPG_IDX_I64 = 1 } spg_index_type;
+typedef enum { SPG_VAL_F64 = 0, SPG_VAL_I32 = 1, SPG_VAL_I64 = 2 } spg_value_type;
+typedef enum { SPG_SIZING_EXACT = 0, SPG_SIZING_LEARNED = 1 } spg_sizing;
+
+/* One CSC matrix.  colptr has ncols + 1 entries of ptr_type; rowidx has nnz
+ * entries of idx_type; vals has nnz entries of val_type.  All device memory,
+ * owned by the caller.  For an output C the library fills ptr_type = I64,
+ * idx_type = the inputs' idx_type and val_type = F64 (double inputs) or I64
+ * (integer inputs; I32 inputs are widened before multiplying). */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    int32_t ptr_type;   /* spg_index_type */
+    int32_t idx_type;   /* spg_index_type */
+    int32_t val_type;   /* spg_value_type */
+    int32_t reserved;
+    void *colptr, *rowidx, *vals;
+} spg_csc;
+
+/* Device-memory callbacks.  alloc returns a device pointer of at least `bytes`
+ * usable in stream order on `stream` (NULL on failure); free releases it.
+ * When both are NULL the library uses cudaMallocAsync / cudaFreeAsync. */
+typedef void *(*spg_alloc_fn)(size_t bytes, void *ctx, void *stream);
+typedef void (*spg_free_fn)(void *ptr, size_t bytes, void *ctx, void *stream);
+
+typedef struct {
+    int32_t P;              /* number of column blocks, >= 1 */
+    int32_t sizing;         /* spg_sizing */
+    int64_t b;              /* fetch-block width in column ids of A, >= 1 */
+    int32_t validate;       /* 1: check that A and B are canonical */
+    int32_t light_max;      /* largest per-column bound handled by the warp hash bins (power of two, 32..1024; 0 = 1024) */
+    int32_t slab_rows;      /* rows per dense slab of the heavy bins (power of two, 1024..16384; 0 = 8192) */
+    int32_t reserved;
+    void *stream;           /* cudaStream_t */
+    spg_alloc_fn alloc;
+    spg_free_fn free;
+    void *alloc_ctx;
+    const void *model;      /* spg_model* for SPG_SIZING_LEARNED, else NULL */
+    double learned_slack;   /* capacity = ceil(slack * predicted nnz) for learned sizing (0 = 1.25) */
+} spg_options;
+
+/* Counters of one plan (filled progressively by plan, symbolic and numeric). */
+typedef struct {
+    int64_t m, k, n, nnzA, nnzB, P, b;
+    int64_t products;            /* sum_j flops_j = <colnnz(A), rownnz(B)> (Section 3.2) */
+    int64_t nnzC;                /* -1 until the symbolic pass ran */
+    int64_t sum_H;               /* sum_i |H_i| */
+    int64_t sum_dtilde;          /* sum_i |D~_i| */
+    int64_t fetch_blocks_total;  /* P * ceil(k / b) */
+    int64_t fetch_blocks_chosen; /* sum_i M_i of Algorithm 2 */
+    int64_t gathered_nnz_exact;  /* nonzeros copied into all A~_i */
+    int64_t gathered_nnz_block;  /* nonzeros inside the chosen fetch blocks (block-granular volume) */
+    int64_t light_columns, heavy_columns, heavy_items, empty_columns;
+    int64_t recomputed_columns;  /* learned sizing: columns that overflowed their predicted capacity */
+    double ms_plan, ms_symbolic, ms_numeric; /* device time of each phase (CUDA events) */
+} spg_stats;
+
+typedef struct spg_plan spg_plan;
+
+/* Fill *opt with defaults: P = 1, b = 1024, exact sizing, validate = 1,
+ * default stream, library allocator. */
+void spgemm_default_options(spg_options *opt);
+
+/*
+ * Steps 1-4 above for all P blocks (Algorithm 1 up to the local multiply,
+ * Algorithm 2).  Reads A and B, allocates and owns the plan's workspace.
+ * Synchronises the stream a few times (to size the workspace).
+ * Errors: SPG_INVALID_ARGUMENT (null, P < 1, b < 1, A.ncols != B.nrows,
+ * bad type codes, mismatched A/B value types), SPG_INVALID_INPUT,
+ * SPG_UNSUPPORTED (m, k, n or the gathered column count >= 2^31),
+ * SPG_OUT_OF_MEMORY, SPG_CUDA_ERROR.  On error *out is NULL.
+ */
+spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_plan **out);
+
+/*
+ * Step 5: exact nnz per column of C.  Writes the n + 1 int64 column pointers
+ * of C into C_colptr (device, caller-allocated, may be NULL to skip) and the
+ * total into *nnzC (host).  Synchronises the stream once (the total is read
+ * back so that the caller can allocate C).
+ */
+spg_status spgemm_symbolic(spg_plan *plan, void *C_colptr, int64_t *nnzC);
+
+/*
+ * Step 6: fill C.  C->colptr must hold the column pointers written by
+ * spgemm_symbolic (int64, n + 1), C->rowidx room for nnzC entries of the
+ * inputs' idx_type and C->vals room for nnzC doubles (double inputs) or int64
+ * (integer inputs).  C's size fields and type codes are set by this call.
+ * Asynchronous (stream-ordered).
+ */
+spg_status spgemm_numeric(spg_plan *plan, spg_csc *C);
+
+/*
+ * plan + symbolic + numeric + destroy in one call.  C's three arrays are
+ * allocated through opt->alloc (or cudaMallocAsync) and belong to the caller
+ * afterwards (release them with the matching free).  With opt->sizing =
+ * SPG_SIZING_LEARNED the symbolic pass is replaced by the model's prediction
+ * and an exact recompute of the columns that overflow; the result is
+ * identical and the call returns SPG_OVERFLOW_RECOMPUTED when any column was
+ * recomputed.
+ */
+spg_status spgemm_1d_multiply(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C);
+
+/* Copy the plan's counters into *st (host).  Synchronises the stream. */
+spg_status spgemm_plan_stats(const spg_plan *plan, spg_stats *st);
+
+/* Release the plan and its workspace (stream-ordered).  NULL is a no-op. */
+spg_status spgemm_plan_destroy(spg_plan *plan);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *spgemm_last_error(void);
+
+/*
+ * Phase inspection for tests: copy planning quantities of block `block` into
+ * caller device buffers (any pointer may be NULL to skip it).
+ *   H_bits      : ceil(k/32) uint32 words, bit h set iff row h of B_i is nonzero
+ *   dtilde      : |D~_i| int32 required column ids, ascending      (*n_dtilde receives |D~_i|)
+ *   fetch       : ceil(k/b) uint8 flags of the chosen fetch blocks
+ *   At_colptr   : |D~_i| + 1 int64 column pointers of A~_i into the plan's
+ *                 gathered arrays (subtract the first entry to index At_rowidx)
+ *   At_rowidx   : int32 rows of A~_i;  At_vals: double or int64 values of A~_i
+ *   flops       : n_i int64 sparse flops of the block's output columns
+ * Synchronises the stream.
+ */
+spg_status spgemm_plan_export(const spg_plan *plan, int32_t block, void *H_bits, void *dtilde,
+                              int64_t *n_dtilde, void *fetch, void *At_colptr, void *At_rowidx,
+                              void *At_vals, void *flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPGEMM1D_H */

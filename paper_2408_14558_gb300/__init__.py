@@ -1,0 +1,338 @@
+"""Python binding of the GB300 sparsity-aware 1D SpGEMM library (libspgemm1d.so).
+
+Argument marshalling only: every step of C = A*B runs in the CUDA kernels behind
+the C ABI declared in ``include/spgemm1d.h``.  PyTorch provides device memory
+(through the allocator callbacks, so the library's workspace comes from the
+caching allocator) and the stream (torch's current stream).  The functions keep
+the C names:
+
+    spgemm_plan, spgemm_symbolic, spgemm_numeric, spgemm_1d_multiply,
+    spgemm_plan_stats, spgemm_plan_destroy, spgemm_last_error,
+    spgemm_plan_export
+
+There is no CPU fallback: if the shared library is missing or fails to load,
+the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspgemm1d.so")
+
+SPG_OK, SPG_INVALID_ARGUMENT, SPG_INVALID_INPUT, SPG_OUT_OF_MEMORY = 0, 1, 2, 3
+SPG_CUDA_ERROR, SPG_TIMEOUT, SPG_UNSUPPORTED, SPG_OVERFLOW_RECOMPUTED = 4, 5, 6, 7
+SPG_IDX_I32, SPG_IDX_I64 = 0, 1
+SPG_VAL_F64, SPG_VAL_I32, SPG_VAL_I64 = 0, 1, 2
+SPG_SIZING_EXACT, SPG_SIZING_LEARNED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_INPUT", 3: "OUT_OF_MEMORY",
+                4: "CUDA_ERROR", 5: "TIMEOUT", 6: "UNSUPPORTED", 7: "OVERFLOW_RECOMPUTED"}
+
+
+class SpgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class spg_csc(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("ptr_type", ctypes.c_int32), ("idx_type", ctypes.c_int32),
+                ("val_type", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("colptr", ctypes.c_void_p), ("rowidx", ctypes.c_void_p), ("vals", ctypes.c_void_p)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class spg_options(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int32), ("sizing", ctypes.c_int32), ("b", ctypes.c_int64),
+                ("validate", ctypes.c_int32), ("light_max", ctypes.c_int32),
+                ("slab_rows", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p), ("model", ctypes.c_void_p),
+                ("learned_slack", ctypes.c_double)]
+
+
+class spg_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "m", "k", "n", "nnzA", "nnzB", "P", "b", "products", "nnzC", "sum_H", "sum_dtilde",
+        "fetch_blocks_total", "fetch_blocks_chosen", "gathered_nnz_exact", "gathered_nnz_block",
+        "light_columns", "heavy_columns", "heavy_items", "empty_columns", "recomputed_columns")] + [
+        ("ms_plan", ctypes.c_double), ("ms_symbolic", ctypes.c_double), ("ms_numeric", ctypes.c_double)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libspgemm1d.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError(f"{path} is missing: build it with paper_2408_14558_gb300.build.build()")
+            lib = ctypes.CDLL(path)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+            lib.spgemm_default_options.argtypes = [ctypes.POINTER(spg_options)]
+            lib.spgemm_default_options.restype = None
+            lib.spgemm_plan.argtypes = [ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc),
+                                        ctypes.POINTER(spg_options), ctypes.POINTER(vp)]
+            lib.spgemm_symbolic.argtypes = [vp, vp, ctypes.POINTER(i64)]
+            lib.spgemm_numeric.argtypes = [vp, ctypes.POINTER(spg_csc)]
+            lib.spgemm_1d_multiply.argtypes = [ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc),
+                                               ctypes.POINTER(spg_options), ctypes.POINTER(spg_csc)]
+            lib.spgemm_plan_stats.argtypes = [vp, ctypes.POINTER(spg_stats)]
+            lib.spgemm_plan_destroy.argtypes = [vp]
+            lib.spgemm_last_error.restype = ctypes.c_char_p
+            lib.spgemm_plan_export.argtypes = [vp, i32, vp, vp, ctypes.POINTER(i64), vp, vp, vp, vp, vp]
+            for name in ("spgemm_plan", "spgemm_symbolic", "spgemm_numeric", "spgemm_1d_multiply",
+                         "spgemm_plan_stats", "spgemm_plan_destroy", "spgemm_plan_export"):
+                getattr(lib, name).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def spgemm_last_error() -> str:
+    return load_library().spgemm_last_error().decode()
+
+
+def _check(status: int):
+    if status not in (SPG_OK, SPG_OVERFLOW_RECOMPUTED):
+        raise SpgError(status, spgemm_last_error())
+    return status
+
+
+# ------------------------------------------------------------------ matrices
+
+_IDX = {torch.int32: SPG_IDX_I32, torch.int64: SPG_IDX_I64}
+_VAL = {torch.float64: SPG_VAL_F64, torch.int32: SPG_VAL_I32, torch.int64: SPG_VAL_I64}
+
+
+@dataclass
+class DeviceCSC:
+    """A CSC matrix whose three arrays are CUDA tensors."""
+    nrows: int
+    ncols: int
+    colptr: torch.Tensor
+    rowidx: torch.Tensor
+    vals: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowidx.numel())
+
+    def as_c(self) -> spg_csc:
+        for t in (self.colptr, self.rowidx, self.vals):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("DeviceCSC arrays must be contiguous CUDA tensors")
+        return spg_csc(self.nrows, self.ncols, self.nnz, _IDX[self.colptr.dtype], _IDX[self.rowidx.dtype],
+                       _VAL[self.vals.dtype], 0, self.colptr.data_ptr(),
+                       self.rowidx.data_ptr() if self.nnz else None, self.vals.data_ptr() if self.nnz else None)
+
+    def to_host(self):
+        """(colptr, rowidx, vals) as numpy arrays."""
+        return self.colptr.cpu().numpy(), self.rowidx.cpu().numpy(), self.vals.cpu().numpy()
+
+
+def to_device(M, device="cuda", ptr_dtype=None, idx_dtype=None, val_dtype=None, pin=False) -> DeviceCSC:
+    """Copy a host CSC (anything with nrows, ncols, colptr, rowidx, vals numpy
+    arrays) to the GPU, optionally converting the array types."""
+    def conv(a, dt):
+        t = torch.from_numpy(a)
+        if dt is not None:
+            t = t.to(dt)
+        if pin:
+            t = t.pin_memory()
+        return t.to(device, non_blocking=pin)
+    return DeviceCSC(int(M.nrows), int(M.ncols), conv(M.colptr, ptr_dtype), conv(M.rowidx, idx_dtype),
+                     conv(M.vals, val_dtype))
+
+
+# --------------------------------------------------------- allocator bridge
+
+class _TorchAllocator:
+    """Device memory for the library from torch's caching allocator."""
+
+    def __init__(self, device):
+        self.device = device
+        self.live = {}
+        self.lock = threading.Lock()
+        self.c_alloc = ALLOC_FN(self._alloc)
+        self.c_free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx, stream):
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        except RuntimeError:
+            return None
+        with self.lock:
+            self.live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(self, ptr, nbytes, ctx, stream):
+        with self.lock:
+            self.live.pop(ptr, None)
+
+    def adopt(self, ptr: int, nbytes: int, dtype, count: int) -> torch.Tensor:
+        """Turn an allocation made through the callback into a typed tensor."""
+        with self.lock:
+            t = self.live.pop(ptr)
+        return t[: count * torch.empty(0, dtype=dtype).element_size()].view(dtype) if count else \
+            torch.empty(0, dtype=dtype, device=self.device)
+
+
+def make_options(P=1, b=1024, stream=None, validate=True, light_max=0, slab_rows=0, sizing=SPG_SIZING_EXACT,
+                 model=None, learned_slack=0.0, allocator=None) -> spg_options:
+    lib = load_library()
+    o = spg_options()
+    lib.spgemm_default_options(ctypes.byref(o))
+    o.P, o.b, o.validate = int(P), int(b), 1 if validate else 0
+    o.light_max, o.slab_rows, o.sizing = int(light_max), int(slab_rows), int(sizing)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    o.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    if allocator is not None:
+        o.alloc, o.free = allocator.c_alloc, allocator.c_free
+    o.model = model
+    if learned_slack:
+        o.learned_slack = float(learned_slack)
+    return o
+
+
+# ----------------------------------------------------------------- the API
+
+class Plan:
+    """Handle of an spg_plan (steps 1-4 done).  Destroy it explicitly with
+    spgemm_plan_destroy, or let garbage collection do it."""
+
+    def __init__(self, handle, A, B, opts, allocator):
+        self.handle = handle
+        self._keep = (A, B, opts, allocator)   # inputs must outlive the plan
+        self.A, self.B = A, B
+        self.nnzC = None
+        self.colptr = None
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                load_library().spgemm_plan_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def spgemm_plan(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, validate=True, light_max=0,
+                slab_rows=0) -> Plan:
+    lib = load_library()
+    alloc = _TorchAllocator(A.colptr.device)
+    opts = make_options(P, b, stream, validate, light_max, slab_rows, allocator=alloc)
+    a, bb = A.as_c(), B.as_c()
+    h = ctypes.c_void_p()
+    _check(lib.spgemm_plan(ctypes.byref(a), ctypes.byref(bb), ctypes.byref(opts), ctypes.byref(h)))
+    return Plan(h, A, B, opts, alloc)
+
+
+def spgemm_symbolic(plan: Plan):
+    """Returns (colptr int64 tensor of n+1, nnz(C))."""
+    lib = load_library()
+    colptr = torch.empty(plan.B.ncols + 1, dtype=torch.int64, device=plan.B.colptr.device)
+    nnz = ctypes.c_int64()
+    _check(lib.spgemm_symbolic(plan.handle, colptr.data_ptr(), ctypes.byref(nnz)))
+    plan.nnzC, plan.colptr = int(nnz.value), colptr
+    return colptr, int(nnz.value)
+
+
+def spgemm_numeric(plan: Plan, colptr: torch.Tensor | None = None) -> DeviceCSC:
+    lib = load_library()
+    if plan.nnzC is None:
+        spgemm_symbolic(plan)
+    colptr = plan.colptr if colptr is None else colptr
+    dev = plan.B.colptr.device
+    idx_dt = plan.A.rowidx.dtype
+    val_dt = torch.float64 if plan.A.vals.dtype == torch.float64 else torch.int64
+    rowidx = torch.empty(plan.nnzC, dtype=idx_dt, device=dev)
+    vals = torch.empty(plan.nnzC, dtype=val_dt, device=dev)
+    c = spg_csc(0, 0, 0, 0, 0, 0, 0, colptr.data_ptr(), rowidx.data_ptr() if plan.nnzC else None,
+                vals.data_ptr() if plan.nnzC else None)
+    _check(lib.spgemm_numeric(plan.handle, ctypes.byref(c)))
+    return DeviceCSC(plan.A.nrows, plan.B.ncols, colptr, rowidx, vals)
+
+
+def spgemm_plan_stats(plan: Plan) -> dict:
+    lib = load_library()
+    st = spg_stats()
+    _check(lib.spgemm_plan_stats(plan.handle, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in spg_stats._fields_}
+
+
+def spgemm_plan_destroy(plan: Plan):
+    if plan.handle:
+        _check(load_library().spgemm_plan_destroy(plan.handle))
+        plan.handle = None
+
+
+def spgemm_1d_multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, validate=True, light_max=0,
+                       slab_rows=0, sizing=SPG_SIZING_EXACT, model=None, learned_slack=0.0):
+    """plan + symbolic + numeric + destroy in one C call; C's arrays come from
+    torch's allocator through the callbacks.  Returns (C, status)."""
+    lib = load_library()
+    alloc = _TorchAllocator(A.colptr.device)
+    opts = make_options(P, b, stream, validate, light_max, slab_rows, sizing,
+                        model.handle if model is not None else None, learned_slack, allocator=alloc)
+    a, bb, c = A.as_c(), B.as_c(), spg_csc()
+    st = _check(lib.spgemm_1d_multiply(ctypes.byref(a), ctypes.byref(bb), ctypes.byref(opts), ctypes.byref(c)))
+    idx_dt = torch.int64 if c.idx_type == SPG_IDX_I64 else torch.int32
+    val_dt = torch.float64 if c.val_type == SPG_VAL_F64 else torch.int64
+    colptr = alloc.adopt(c.colptr, 0, torch.int64, c.ncols + 1)
+    rowidx = alloc.adopt(c.rowidx, 0, idx_dt, c.nnz)
+    vals = alloc.adopt(c.vals, 0, val_dt, c.nnz)
+    return DeviceCSC(c.nrows, c.ncols, colptr, rowidx, vals), st
+
+
+def spgemm_plan_export(plan: Plan, block: int) -> dict:
+    """Planning quantities of one column block as CUDA tensors (for tests)."""
+    lib = load_library()
+    dev = plan.B.colptr.device
+    k, n = plan.B.nrows, plan.B.ncols
+    P = plan._keep[2].P
+    b = plan._keep[2].b
+    W = (k + 31) // 32
+    nfb = (k + b - 1) // b
+    c0, c1 = block * n // P, (block + 1) * n // P
+    H = torch.zeros(max(W, 1), dtype=torch.int32, device=dev)
+    nd = ctypes.c_int64()
+    _check(lib.spgemm_plan_export(plan.handle, block, H.data_ptr(), None, ctypes.byref(nd), None, None, None,
+                                  None, None))
+    nd = int(nd.value)
+    dt = torch.zeros(max(nd, 1), dtype=torch.int32, device=dev)
+    fetch = torch.zeros(max(nfb, 1), dtype=torch.uint8, device=dev)
+    acp = torch.zeros(nd + 1, dtype=torch.int64, device=dev)
+    fl = torch.zeros(max(c1 - c0, 1), dtype=torch.int64, device=dev)
+    _check(lib.spgemm_plan_export(plan.handle, block, None, dt.data_ptr(), None, fetch.data_ptr(),
+                                  acp.data_ptr(), None, None, fl.data_ptr()))
+    vol = int((acp[-1] - acp[0]).item())
+    rows = torch.zeros(max(vol, 1), dtype=torch.int32, device=dev)
+    vdt = torch.float64 if plan.A.vals.dtype == torch.float64 else torch.int64
+    vals = torch.zeros(max(vol, 1), dtype=vdt, device=dev)
+    _check(lib.spgemm_plan_export(plan.handle, block, None, None, None, None, None, rows.data_ptr(),
+                                  vals.data_ptr(), None))
+    return {"H_bits": H[:W], "dtilde": dt[:nd], "fetch": fetch[:nfb], "At_colptr": acp - acp[0],
+            "At_rowidx": rows[:vol], "At_vals": vals[:vol], "flops": fl[: c1 - c0]}
+
+
+def multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, **kw) -> DeviceCSC:
+    """Convenience: plan, symbolic, allocate C with torch, numeric, destroy."""
+    plan = spgemm_plan(A, B, P, b, **kw)
+    try:
+        spgemm_symbolic(plan)
+        return spgemm_numeric(plan)
+    finally:
+        spgemm_plan_destroy(plan)

@@ -1,0 +1,334 @@
+// Numeric pass: the rows and values of C (Algorithm 1, local multiply
+// C_i = A~_i * B_i, Gustavson column by column), written at the column
+// pointers produced by the symbolic pass.
+//   light bins: one warp per column, shared open-addressing table of
+//               (row, value) sized >= 2 x nnz_j; afterwards the occupied slots
+//               are compacted in place and sorted by row (bitonic network)
+//   heavy bin:  one CTA per (column, row slab): the symbolic bitmap of the
+//               slab gives every present row its rank, products accumulate at
+//               acc[rank] in shared memory, and the slab is written out in row
+//               order with no sort
+#include "spg_internal.cuh"
+
+namespace spg {
+
+// Exclusive scan of popc(bits[w]) over the RW words of a slab by the whole CTA.
+// Writes pre[0..RW) and returns the total to every thread.
+__device__ __forceinline__ int cta_scan_popc(const uint32_t *bits, int *pre, int RW, int *wsum) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int per = (RW + nt - 1) / nt;
+    const int w0 = tid * per;
+    int local = 0;
+    for (int w = w0; w < min(RW, w0 + per); w++) local += __popc(bits[w]);
+    const int lane = tid & 31, wid = tid >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = nt >> 5;
+        int v = lane < nw ? wsum[lane] : 0;
+        int vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(kFull, vi, o);
+            if (lane >= o) vi += t;
+        }
+        if (lane < nw) wsum[lane] = vi - v;
+        if (lane == 31) wsum[32] = vi;
+    }
+    __syncthreads();
+    int run = wsum[wid] + incl - local;
+    for (int w = w0; w < min(RW, w0 + per); w++) {
+        pre[w] = run;
+        run += __popc(bits[w]);
+    }
+    int total = wsum[32];
+    __syncthreads();
+    return total;
+}
+
+// Sort keys[0..npad) ascending (npad a power of two), carrying vals along.
+template <typename Acc>
+__device__ __forceinline__ void warp_bitonic(int *keys, Acc *vals, int npad, int lane) {
+    for (int kk = 2; kk <= npad; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int t = lane; t < (npad >> 1); t += 32) {
+                int i = 2 * jj * (t / jj) + (t % jj);
+                int l = i + jj;
+                bool up = (i & kk) == 0;
+                int ki = keys[i], kl = keys[l];
+                if ((ki > kl) == up) {
+                    keys[i] = kl;
+                    keys[l] = ki;
+                    Acc tv = vals[i];
+                    vals[i] = vals[l];
+                    vals[l] = tv;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <int LOGS, int WARPS, typename Acc, typename OutIdx>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_num_light(const int32_t *__restrict__ list, int64_t ncols, const void *Bcolptr, int p64,
+                const int32_t *__restrict__ Bq, const Acc *__restrict__ Bv, const int64_t *__restrict__ At_colptr,
+                const int32_t *__restrict__ At_row, const Acc *__restrict__ At_val,
+                const int64_t *__restrict__ Ccolptr, OutIdx *__restrict__ Crow, Acc *__restrict__ Cval, int *err) {
+    constexpr int S = 1 << LOGS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSeg<Acc> *segs = (WarpSeg<Acc> *)smem_raw;
+    Acc *vals_all = (Acc *)(segs + WARPS);
+    int *keys_all = (int *)(vals_all + WARPS * S);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int *keys = keys_all + wid * S;
+    Acc *vals = vals_all + wid * S;
+    for (int64_t c = (int64_t)blockIdx.x * WARPS + wid; c < ncols; c += (int64_t)gridDim.x * WARPS) {
+        const int j = list[c];
+        for (int s = lane; s < S; s += 32) {
+            keys[s] = kEmptyKey;
+            vals[s] = Acc(0);
+        }
+        __syncwarp();
+        const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
+        bool full = false;
+        warp_products<true, Acc>(
+            p0, p1, lane, segs[wid], At_row, At_val,
+            [&](int64_t p, long long &st, int &len, Acc &bv) {
+                int q = Bq[p];
+                if (q >= 0) {
+                    st = At_colptr[q];
+                    len = (int)(At_colptr[q + 1] - st);
+                    bv = Bv[p];
+                }
+            },
+            [&](int r, Acc v) {
+                bool fresh;
+                int slot = hash_insert(keys, LOGS, r, &fresh);
+                if (slot < 0)
+                    full = true;
+                else
+                    atomic_add_acc(vals + slot, v);
+            });
+        __syncwarp();
+        // compact the occupied slots to the front: a write never reaches a slot
+        // of a later, still unread chunk because the count so far is <= c0
+        int nout = 0;
+        for (int c0 = 0; c0 < S; c0 += 32) {
+            int kk = keys[c0 + lane];
+            Acc vv = vals[c0 + lane];
+            bool occ = kk != kEmptyKey;
+            unsigned bal = __ballot_sync(kFull, occ);
+            __syncwarp();
+            if (occ) {
+                int pos = nout + __popc(bal & ((1u << lane) - 1u));
+                keys[pos] = kk;
+                vals[pos] = vv;
+            }
+            nout += __popc(bal);
+            __syncwarp();
+        }
+        int npad = 1;
+        while (npad < nout) npad <<= 1;
+        for (int s = nout + lane; s < npad; s += 32) keys[s] = INT32_MAX;
+        __syncwarp();
+        warp_bitonic<Acc>(keys, vals, npad, lane);
+        const int64_t base = Ccolptr[j];
+        if ((int64_t)nout != Ccolptr[j + 1] - base) full = true;
+        else
+            for (int s = lane; s < nout; s += 32) {
+                Crow[base + s] = (OutIdx)keys[s];
+                Cval[base + s] = vals[s];
+            }
+        if (__any_sync(kFull, full) && lane == 0) atomicOr(err, kDevErrInternal);
+        __syncwarp();
+    }
+}
+
+template <typename Acc, typename OutIdx>
+__global__ void __launch_bounds__(256)
+    k_num_heavy(int64_t nitems, const int32_t *__restrict__ item_col, const int32_t *__restrict__ item_slab,
+                const int32_t *__restrict__ item_cnt, const int64_t *__restrict__ item_off,
+                const uint32_t *__restrict__ hbits, const void *Bcolptr, int p64, const int32_t *__restrict__ Bq,
+                const Acc *__restrict__ Bv, const int64_t *__restrict__ At_colptr,
+                const int32_t *__restrict__ At_row, const Acc *__restrict__ At_val,
+                const int32_t *__restrict__ split, int T, int R, const int64_t *__restrict__ Ccolptr,
+                OutIdx *__restrict__ Crow, Acc *__restrict__ Cval, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int RW = R >> 5;
+    const int nw = blockDim.x >> 5;
+    WarpSeg<Acc> *segs = (WarpSeg<Acc> *)smem_raw;
+    Acc *acc = (Acc *)(segs + nw);
+    uint32_t *bits = (uint32_t *)(acc + R);
+    int *pre = (int *)(bits + RW);
+    __shared__ int wsum[33];
+    __shared__ int bad_sh;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) bad_sh = 0;
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int j = item_col[it], t = item_slab[it];
+        const uint32_t *src = hbits + it * RW;
+        for (int w = threadIdx.x; w < RW; w += blockDim.x) bits[w] = src[w];
+        __syncthreads();
+        const int cnt = cta_scan_popc(bits, pre, RW, wsum);
+        if (cnt != item_cnt[it]) {
+            // the slab's room in C was sized from item_cnt: never write past it
+            if (threadIdx.x == 0) bad_sh = 1;
+            __syncthreads();
+            continue;
+        }
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) acc[i] = Acc(0);
+        __syncthreads();
+        const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
+        const int wbase = t * RW;
+        bool miss = false;
+        for (int64_t c0 = p0 + (int64_t)wid * 32; c0 < p1; c0 += (int64_t)nw * 32) {
+            warp_products<true, Acc>(
+                c0, min(c0 + 32, p1), lane, segs[wid], At_row, At_val,
+                [&](int64_t p, long long &st, int &len, Acc &bv) {
+                    int q = Bq[p];
+                    if (q >= 0) {
+                        const int32_t *sp = split + (int64_t)q * (T + 1) + t;
+                        int a = sp[0], b = sp[1];
+                        st = At_colptr[q] + a;
+                        len = b - a;
+                        bv = Bv[p];
+                    }
+                },
+                [&](int r, Acc v) {
+                    int w = (r >> 5) - wbase;
+                    uint32_t word = bits[w];
+                    uint32_t below = word & ((1u << (r & 31)) - 1u);
+                    if (!((word >> (r & 31)) & 1u)) miss = true;
+                    else atomic_add_acc(acc + pre[w] + __popc(below), v);
+                });
+        }
+        if (miss) bad_sh = 1;
+        __syncthreads();
+        const int64_t base = Ccolptr[j] + item_off[it];
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) Cval[base + i] = acc[i];
+        const OutIdx rbase = (OutIdx)t * R;
+        for (int w = threadIdx.x; w < RW; w += blockDim.x) {
+            uint32_t word = bits[w];
+            int64_t pos = base + pre[w];
+            while (word) {
+                int bb = __ffs(word) - 1;
+                Crow[pos++] = rbase + (OutIdx)(w * 32 + bb);
+                word &= word - 1u;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && bad_sh) atomicOr(err, kDevErrInternal);
+}
+
+__global__ void k_rebin_numeric(const int8_t *bin_sym, const int64_t *nnzcol, int64_t n, int8_t *bin_num) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        int b = bin_sym[j];
+        if (b != kBinHeavy && b != kBinEmpty) {
+            long long U = nnzcol[j];
+            if (U <= 0) {
+                b = kBinEmpty;
+            } else {
+                long long S = 64;
+                b = 1;
+                while (S < 2 * U) {
+                    S <<= 1;
+                    b++;
+                }
+            }
+        }
+        bin_num[j] = (int8_t)b;
+    }
+}
+
+template <int LOGS, int WARPS, typename Acc, typename OutIdx>
+static spg_status launch_num_light(spg_plan *p, const int32_t *list, int64_t cnt, spg_csc *C) {
+    size_t smem = sizeof(WarpSeg<Acc>) * WARPS + (sizeof(Acc) + sizeof(int)) * (size_t)WARPS * (1 << LOGS);
+    auto kern = k_num_light<LOGS, WARPS, Acc, OutIdx>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WARPS * 32, smem);
+    if (occ < 1) occ = 1;
+    int g = grid_for(cnt, WARPS, p->sm_count * occ);
+    kern<<<g, WARPS * 32, smem, p->st>>>(list, cnt, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq,
+                                         (const Acc *)p->Bv, p->At_colptr, p->At_row, (const Acc *)p->At_val,
+                                         p->Ccolptr, (OutIdx *)C->rowidx, (Acc *)C->vals, p->d_err);
+    return cuda_check(cudaGetLastError(), "numeric light");
+}
+
+template <typename Acc, typename OutIdx>
+static spg_status numeric_typed(spg_plan *p, spg_csc *C) {
+    spg_status s = SPG_OK;
+    for (int bin = 1; bin <= kMaxLightBin && !s; bin++) {
+        int64_t cnt = p->nbin_off[bin + 1] - p->nbin_off[bin];
+        if (cnt == 0) continue;
+        const int32_t *list = p->nbinlist + p->nbin_off[bin];
+        switch (bin) {
+            case 1: s = launch_num_light<6, 8, Acc, OutIdx>(p, list, cnt, C); break;
+            case 2: s = launch_num_light<7, 8, Acc, OutIdx>(p, list, cnt, C); break;
+            case 3: s = launch_num_light<8, 8, Acc, OutIdx>(p, list, cnt, C); break;
+            case 4: s = launch_num_light<9, 8, Acc, OutIdx>(p, list, cnt, C); break;
+            case 5: s = launch_num_light<10, 4, Acc, OutIdx>(p, list, cnt, C); break;
+            default: s = launch_num_light<11, 4, Acc, OutIdx>(p, list, cnt, C); break;
+        }
+    }
+    if (s) return s;
+    if (p->nitems > 0) {
+        const int threads = 256;
+        const int RW = p->R / 32;
+        size_t smem = sizeof(WarpSeg<Acc>) * (threads / 32) + sizeof(Acc) * (size_t)p->R +
+                      sizeof(uint32_t) * (size_t)RW + sizeof(int) * (size_t)(RW + 2);
+        auto kern = k_num_heavy<Acc, OutIdx>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int occ = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+        if (occ < 1) occ = 1;
+        int g = grid_for(p->nitems, 1, p->sm_count * occ);
+        kern<<<g, threads, smem, p->st>>>(p->nitems, p->item_col, p->item_slab, p->item_cnt, p->item_off, p->hbits,
+                                          p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv,
+                                          p->At_colptr, p->At_row, (const Acc *)p->At_val, p->split, p->T, p->R,
+                                          p->Ccolptr, (OutIdx *)C->rowidx, (Acc *)C->vals, p->d_err);
+        s = cuda_check(cudaGetLastError(), "numeric heavy");
+    }
+    return s;
+}
+
+spg_status run_numeric(spg_plan *p, spg_csc *C) {
+    cudaStream_t st = p->st;
+    const int64_t n = p->n;
+    if (!p->nbinlist) {
+        int8_t *bn = (int8_t *)ws_alloc(p, (size_t)(n + 1));
+        p->nbinlist = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(n + 1));
+        if (!bn || !p->nbinlist) return SPG_OUT_OF_MEMORY;
+        if (n > 0) {
+            k_rebin_numeric<<<grid_for(n, 256, p->sm_count * 8), 256, 0, st>>>(p->bin_of, p->nnzcol, n, bn);
+            spg_status s = cuda_check(cudaGetLastError(), "rebin");
+            if (s) return s;
+            s = bin_columns(p, bn, p->nbinlist, p->nbin_off);
+            if (s) return s;
+        }
+    }
+    if (C->colptr && C->colptr != (void *)p->Ccolptr) {
+        spg_status s = cuda_check(cudaMemcpyAsync(C->colptr, p->Ccolptr, sizeof(int64_t) * (size_t)(n + 1),
+                                                  cudaMemcpyDeviceToDevice, st),
+                                  "colptr copy");
+        if (s) return s;
+    }
+    cudaEventRecord(p->ev[4], st);
+    spg_status s;
+    if (p->acc_f64)
+        s = p->out_idx64 ? numeric_typed<double, long long>(p, C) : numeric_typed<double, int>(p, C);
+    else
+        s = p->out_idx64 ? numeric_typed<long long, long long>(p, C) : numeric_typed<long long, int>(p, C);
+    cudaEventRecord(p->ev[5], st);
+    return s;
+}
+
+}  // namespace spg

@@ -1,0 +1,821 @@
+// Planning phase of the sparsity-aware 1D SpGEMM: steps 1-4 of Algorithm 1
+// for all P column blocks at once, on one GPU.
+//   k_nonempty_bits  D, the nonempty columns of A (Algorithm 1, allgather of
+//                    nonzero column ids: here A.colptr is local)
+//   k_mark_H         H_i, nonzero rows of B_i (Table 1, Algorithm 1)
+//   k_popc_HD        popc(H_i & D) per word, then a scan gives each required
+//                    column its place in D~ (Algorithm 1, D~ = H_i AND D)
+//   k_dtilde         the ascending list D~_i
+//   k_fetch          Algorithm 2 with groups of b consecutive column ids
+//   k_gather_len / k_gather_copy   A~_i = A(:, D~_i); one CTA per chosen fetch
+//                    block (the single-GPU analogue of one MPI_Get per group)
+//   k_remap_B        B_i's rows k -> column of A~_i (Algorithm 1's local index)
+//   k_col_stats      flops_j (Section 3.2), row window, features, bin id
+//   k_split          heavy bins: per A~ column, the first entry of every row slab
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "spg_internal.cuh"
+
+namespace spg {
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+const char *last_error_str() { return g_last_error.c_str(); }
+void clear_error() { g_last_error.clear(); }
+
+spg_status cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SPG_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return SPG_OUT_OF_MEMORY;
+    return SPG_CUDA_ERROR;
+}
+
+// --------------------------------------------------------------- workspace
+
+void *ws_alloc(spg_plan *p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *ptr = nullptr;
+    if (p->opt.alloc) {
+        ptr = p->opt.alloc(bytes, p->opt.alloc_ctx, (void *)p->st);
+    } else {
+        if (cudaMallocAsync(&ptr, bytes, p->st) != cudaSuccess) {
+            cudaGetLastError();
+            ptr = nullptr;
+        }
+    }
+    if (!ptr) {
+        set_error("workspace allocation of %zu bytes failed", bytes);
+        return nullptr;
+    }
+    p->allocs.push_back({ptr, bytes});
+    return ptr;
+}
+
+void ws_free_all(spg_plan *p) {
+    for (auto &a : p->allocs) {
+        if (p->opt.free)
+            p->opt.free(a.p, a.bytes, p->opt.alloc_ctx, (void *)p->st);
+        else if (!p->opt.alloc)
+            cudaFreeAsync(a.p, p->st);
+    }
+    p->allocs.clear();
+}
+
+int grid_for(int64_t work, int per_block, int max_blocks) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+spg_status read_dev_err(spg_plan *p, const char *phase) {
+    // the error word lands in the last pinned slot so that other read-backs
+    // queued before this call stay intact
+    int64_t *slot = p->h_pinned + 63;
+    *slot = 0;
+    spg_status s = cuda_check(
+        cudaMemcpyAsync(slot, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->st), phase);
+    if (s) return s;
+    s = cuda_check(cudaStreamSynchronize(p->st), phase);
+    if (s) return s;
+    int e = *(int *)slot;
+    if (e & kDevErrInput) {
+        set_error("%s: input matrix is not canonical CSC (colptr not monotone, or a row id out of range, unsorted or repeated)", phase);
+        return SPG_INVALID_INPUT;
+    }
+    if (e & kDevErrRange) {
+        set_error("%s: a size limit was exceeded", phase);
+        return SPG_UNSUPPORTED;
+    }
+    if (e & kDevErrInternal) {
+        set_error("%s: internal consistency check failed", phase);
+        return SPG_CUDA_ERROR;
+    }
+    return SPG_OK;
+}
+
+// ------------------------------------------------------------------ kernels
+
+// Device counters in plan->d_cnt.
+enum {
+    kCntSumH = 0,
+    kCntProducts = 1,
+    kCntFetchChosen = 2,
+    kCntVolBlock = 3,
+    kCntMaxAcol = 4,
+    kCntBin0 = 8,  // kNumBins histogram counters
+    kCntHeavyItems = 16,
+    kCntSlots = 24
+};
+
+__global__ void k_validate(const void *colptr, int p64, const void *rowidx, int i64, int64_t nrows,
+                           int64_t ncols, int64_t nnz, int *err) {
+    int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (warp == 0 && lane == 0) {
+        if (ld_ptr(colptr, p64, 0) != 0 || ld_ptr(colptr, p64, ncols) != nnz) atomicOr(err, kDevErrInput);
+    }
+    for (int64_t j = warp; j < ncols; j += nwarps) {
+        int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
+        bool bad = (s > e) || (s < 0) || (e > nnz);
+        if (!bad) {
+            for (int64_t q = s + lane; q < e; q += 32) {
+                int64_t r = ld_ptr(rowidx, i64, q);
+                if (r < 0 || r >= nrows) bad = true;
+                if (q > s && ld_ptr(rowidx, i64, q - 1) >= r) bad = true;
+            }
+        }
+        if (__any_sync(kFull, bad) && lane == 0) atomicOr(err, kDevErrInput);
+    }
+}
+
+__global__ void k_nonempty_bits(const void *colptr, int p64, int64_t k, int64_t W, uint32_t *D) {
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < W;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t bits = 0;
+        int64_t h0 = w * 32;
+        int64_t prev = ld_ptr(colptr, p64, h0);
+        for (int bb = 0; bb < 32 && h0 + bb < k; bb++) {
+            int64_t nx = ld_ptr(colptr, p64, h0 + bb + 1);
+            if (nx > prev) bits |= 1u << bb;
+            prev = nx;
+        }
+        D[w] = bits;
+    }
+}
+
+// Warp per column j of B: set bit r of H_{block(j)} for every stored row r.
+__global__ void k_mark_H(const void *colptr, int p64, const void *rowidx, int i64, int64_t n, int P,
+                         int64_t W, uint32_t *H) {
+    int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = warp; j < n; j += nwarps) {
+        int i = block_of(j, n, P);
+        uint32_t *Hi = H + (int64_t)i * W;
+        int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
+        for (int64_t q = s + lane; q < e; q += 32) {
+            int64_t r = ld_ptr(rowidx, i64, q);
+            atomicOr(Hi + (r >> 5), 1u << (r & 31));
+        }
+    }
+}
+
+// cnt[i*W + w] = popc(H_i[w] & D[w]); also sum_i |H_i| for the statistics.
+__global__ void k_popc_HD(const uint32_t *H, const uint32_t *D, int64_t W, int64_t total,
+                          int32_t *cnt, long long *sumH) {
+    long long h = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t hw = H[x];
+        cnt[x] = __popc(hw & D[x % W]);
+        h += __popc(hw);
+    }
+    h = warp_sum_ll(h);
+    if ((threadIdx.x & 31) == 0 && h) atomicAdd((unsigned long long *)sumH, (unsigned long long)h);
+}
+
+// Global index in D~ of the first required column >= x in block i.
+__device__ __forceinline__ int64_t rank_at(const uint32_t *H, const uint32_t *D, const int64_t *rankpre,
+                                           int64_t W, int i, int64_t x) {
+    int64_t w = x >> 5;
+    int64_t r = rankpre[(int64_t)i * W + w];
+    if (x & 31) r += __popc(H[(int64_t)i * W + w] & D[w] & ((1u << (x & 31)) - 1u));
+    return r;
+}
+
+__global__ void k_dtilde(const uint32_t *H, const uint32_t *D, const int64_t *rankpre, int64_t W,
+                         int64_t total, int32_t *dtilde) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int64_t w = x % W;
+        uint32_t bits = H[x] & D[w];
+        int64_t base = rankpre[x];
+        while (bits) {
+            int bb = __ffs(bits) - 1;
+            dtilde[base++] = (int32_t)(w * 32 + bb);
+            bits &= bits - 1;
+        }
+    }
+}
+
+// Algorithm 2: fetch block t of block i is chosen iff it contains a required column.
+__global__ void k_fetch(const uint32_t *H, const uint32_t *D, const int64_t *rankpre, int64_t W,
+                        int64_t k, int64_t b, int64_t nfb, int P, const void *Acolptr, int p64,
+                        uint8_t *fetch, long long *chosen, long long *volblock) {
+    long long c = 0, v = 0;
+    int64_t total = nfb * P;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(x / nfb);
+        int64_t t = x % nfb;
+        int64_t lo = t * b, hi = min(k, lo + b);
+        bool f = rank_at(H, D, rankpre, W, i, hi) > rank_at(H, D, rankpre, W, i, lo);
+        fetch[x] = f ? 1 : 0;
+        if (f) {
+            c++;
+            v += ld_ptr(Acolptr, p64, hi) - ld_ptr(Acolptr, p64, lo);
+        }
+    }
+    c = warp_sum_ll(c);
+    v = warp_sum_ll(v);
+    if ((threadIdx.x & 31) == 0) {
+        if (c) atomicAdd((unsigned long long *)chosen, (unsigned long long)c);
+        if (v) atomicAdd((unsigned long long *)volblock, (unsigned long long)v);
+    }
+}
+
+__global__ void k_gather_len(const int32_t *dtilde, int64_t ndt, const void *Acolptr, int p64,
+                             int64_t *len, long long *maxlen) {
+    long long mx = 0;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ndt;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int64_t h = dtilde[g];
+        int64_t l = ld_ptr(Acolptr, p64, h + 1) - ld_ptr(Acolptr, p64, h);
+        len[g] = l;
+        mx = max(mx, (long long)l);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax((unsigned long long *)maxlen, (unsigned long long)mx);
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc load_val(const void *v, int vt, int64_t i);
+template <>
+__device__ __forceinline__ double load_val<double>(const void *v, int, int64_t i) {
+    return __ldg((const double *)v + i);
+}
+template <>
+__device__ __forceinline__ long long load_val<long long>(const void *v, int vt, int64_t i) {
+    return vt == SPG_VAL_I32 ? (long long)__ldg((const int *)v + i) : (long long)__ldg((const long long *)v + i);
+}
+
+// One CTA per chosen fetch block (i, t): copy the required columns it holds
+// into A~ (rows narrowed to int32, values widened to the accumulation type).
+template <typename Acc>
+__global__ void k_gather_copy(const uint32_t *H, const uint32_t *D, const int64_t *rankpre, int64_t W,
+                              int64_t k, int64_t b, int64_t nfb, int P, const uint8_t *fetch,
+                              const int32_t *dtilde, const void *Acolptr, int p64, const void *Arow,
+                              int i64, const void *Aval, int vt, const int64_t *At_colptr,
+                              int32_t *At_row, Acc *At_val) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t units = nfb * P;
+    for (int64_t x = blockIdx.x; x < units; x += gridDim.x) {
+        if (!fetch[x]) continue;
+        int i = (int)(x / nfb);
+        int64_t t = x % nfb;
+        int64_t lo = t * b, hi = min(k, lo + b);
+        int64_t g0 = rank_at(H, D, rankpre, W, i, lo), g1 = rank_at(H, D, rankpre, W, i, hi);
+        for (int64_t g = g0 + wid; g < g1; g += nw) {
+            int64_t h = dtilde[g];
+            int64_t src = ld_ptr(Acolptr, p64, h);
+            int64_t dst = At_colptr[g];
+            int64_t len = At_colptr[g + 1] - dst;
+            for (int64_t e = lane; e < len; e += 32) {
+                At_row[dst + e] = (int32_t)ld_ptr(Arow, i64, src + e);
+                At_val[dst + e] = load_val<Acc>(Aval, vt, src + e);
+            }
+        }
+    }
+}
+
+// Warp per column j: each row k of B_i becomes its column index in A~ (or -1).
+template <typename Acc>
+__global__ void k_remap_B(const void *colptr, int p64, const void *rowidx, int i64, const void *vals,
+                          int vt, int64_t n, int P, const uint32_t *H, const uint32_t *D,
+                          const int64_t *rankpre, int64_t W, int32_t *Bq, Acc *Bv) {
+    int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = warp; j < n; j += nwarps) {
+        int i = block_of(j, n, P);
+        int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
+        for (int64_t q = s + lane; q < e; q += 32) {
+            int64_t r = ld_ptr(rowidx, i64, q);
+            int64_t w = r >> 5;
+            uint32_t word = H[(int64_t)i * W + w] & D[w];
+            int32_t loc = -1;
+            if ((word >> (r & 31)) & 1u)
+                loc = (int32_t)(rankpre[(int64_t)i * W + w] + __popc(word & ((1u << (r & 31)) - 1u)));
+            Bq[q] = loc;
+            Bv[q] = load_val<Acc>(vals, vt, q);
+        }
+    }
+}
+
+__device__ __forceinline__ int light_bin(long long U, int light_max) {
+    if (U <= 0) return kBinEmpty;
+    if (U > light_max) return kBinHeavy;
+    // table size S = max(64, next power of two >= 2U); bin = log2(S) - 5
+    long long S = 64;
+    int bin = 1;
+    while (S < 2 * U) {
+        S <<= 1;
+        bin++;
+    }
+    return bin;
+}
+
+// Warp per output column: flops_j, the row window of its products, the MLP
+// features and the symbolic bin (bound U = min(flops_j, window)).
+__global__ void k_col_stats(const void *Bcolptr, int p64, int64_t n, const int32_t *Bq,
+                            const int64_t *At_colptr, const int32_t *At_row, int light_max,
+                            int64_t *flops, int32_t *win_lo, int32_t *win_hi, int32_t *nnzb,
+                            int32_t *maxa, int8_t *bin_of, long long *bincnt, long long *products) {
+    __shared__ int hist[kNumBins];
+    __shared__ long long prod_sh;
+    if (threadIdx.x < kNumBins) hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) prod_sh = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    long long prod_local = 0;
+    for (int64_t j = warp; j < n; j += nwarps) {
+        int64_t s = ld_ptr(Bcolptr, p64, j), e = ld_ptr(Bcolptr, p64, j + 1);
+        long long fl = 0;
+        int mx = 0, lo = INT32_MAX, hi = -1;
+        for (int64_t q = s + lane; q < e; q += 32) {
+            int loc = Bq[q];
+            if (loc >= 0) {
+                int64_t a0 = At_colptr[loc], a1 = At_colptr[loc + 1];
+                int len = (int)(a1 - a0);
+                fl += len;
+                mx = max(mx, len);
+                if (len > 0) {
+                    lo = min(lo, At_row[a0]);
+                    hi = max(hi, At_row[a1 - 1]);
+                }
+            }
+        }
+        fl = warp_sum_ll(fl);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+            lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+            hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+        }
+        if (lane == 0) {
+            flops[j] = fl;
+            win_lo[j] = fl ? lo : 0;
+            win_hi[j] = fl ? hi : -1;
+            nnzb[j] = (int32_t)(e - s);
+            maxa[j] = mx;
+            long long U = fl ? min(fl, (long long)(hi - lo + 1)) : 0;
+            int bin = light_bin(U, light_max);
+            bin_of[j] = (int8_t)bin;
+            atomicAdd(&hist[bin], 1);
+            prod_local += fl;
+        }
+    }
+    if (lane == 0 && prod_local) atomicAdd((unsigned long long *)&prod_sh, (unsigned long long)prod_local);
+    __syncthreads();
+    if (threadIdx.x < kNumBins && hist[threadIdx.x])
+        atomicAdd((unsigned long long *)&bincnt[threadIdx.x], (unsigned long long)hist[threadIdx.x]);
+    if (threadIdx.x == 0 && prod_sh) atomicAdd((unsigned long long *)products, (unsigned long long)prod_sh);
+}
+
+__global__ void k_bin_hist(const int8_t *bin_of, int64_t n, long long *bincnt) {
+    __shared__ int hist[kNumBins];
+    if (threadIdx.x < kNumBins) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hist[bin_of[j]], 1);
+    __syncthreads();
+    if (threadIdx.x < kNumBins && hist[threadIdx.x])
+        atomicAdd((unsigned long long *)&bincnt[threadIdx.x], (unsigned long long)hist[threadIdx.x]);
+}
+
+// Counting sort of column ids by bin: a CTA reserves one range per bin with a
+// single global atomic, then places its columns inside it.
+__global__ void k_bin_scatter(const int8_t *bin_of, int64_t n, long long *cursor, int32_t *list) {
+    __shared__ int cnt[kNumBins];
+    __shared__ long long base[kNumBins];
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < n; j0 += (int64_t)gridDim.x * blockDim.x) {
+        if (threadIdx.x < kNumBins) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        int64_t j = j0 + threadIdx.x;
+        int bin = -1, local = 0;
+        if (j < n) {
+            bin = bin_of[j];
+            local = atomicAdd(&cnt[bin], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumBins && cnt[threadIdx.x])
+            base[threadIdx.x] = (long long)atomicAdd((unsigned long long *)&cursor[threadIdx.x],
+                                                     (unsigned long long)cnt[threadIdx.x]);
+        __syncthreads();
+        if (bin >= 0) list[base[bin] + local] = (int32_t)j;
+        __syncthreads();
+    }
+}
+
+spg_status bin_columns(spg_plan *p, const int8_t *bin_of, int32_t *list, int64_t *off_host) {
+    int64_t n = p->n;
+    long long *cnt = (long long *)(p->d_cnt + kCntBin0);
+    spg_status s = cuda_check(cudaMemsetAsync(cnt, 0, sizeof(long long) * kNumBins, p->st), "bin memset");
+    if (s) return s;
+    int g = grid_for(n, 256, p->sm_count * 8);
+    k_bin_hist<<<g, 256, 0, p->st>>>(bin_of, n, cnt);
+    s = cuda_check(cudaMemcpyAsync(p->h_pinned, cnt, sizeof(long long) * kNumBins, cudaMemcpyDeviceToHost, p->st),
+                   "bin readback");
+    if (s) return s;
+    s = cuda_check(cudaStreamSynchronize(p->st), "bin readback");
+    if (s) return s;
+    off_host[0] = 0;
+    for (int b = 0; b < kNumBins; b++) off_host[b + 1] = off_host[b] + p->h_pinned[b];
+    for (int b = 0; b < kNumBins; b++) p->h_pinned[b] = off_host[b];
+    s = cuda_check(cudaMemcpyAsync(p->d_bincur, p->h_pinned, sizeof(long long) * kNumBins,
+                                   cudaMemcpyHostToDevice, p->st), "bin cursor upload");
+    if (s) return s;
+    k_bin_scatter<<<g, 256, 0, p->st>>>(bin_of, n, (long long *)p->d_bincur, list);
+    s = cuda_check(cudaGetLastError(), "bin scatter");
+    if (s) return s;
+    // the pinned buffer is reused by the next read-back: make sure the upload consumed it
+    return cuda_check(cudaStreamSynchronize(p->st), "bin scatter");
+}
+
+// Heavy bins: slabs [t_lo, t_hi] of every heavy column from its row window.
+__global__ void k_heavy_nslab(const int32_t *list, int64_t nheavy, const int32_t *win_lo,
+                              const int32_t *win_hi, int R, int64_t *nslab) {
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += (int64_t)gridDim.x * blockDim.x) {
+        int j = list[h];
+        nslab[h] = (int64_t)(win_hi[j] / R - win_lo[j] / R + 1);
+    }
+}
+
+__global__ void k_heavy_items(const int32_t *list, int64_t nheavy, const int32_t *win_lo, int R,
+                              const int64_t *item_first, int32_t *item_col, int32_t *item_slab) {
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += (int64_t)gridDim.x * blockDim.x) {
+        int j = list[h];
+        int t0 = win_lo[j] / R;
+        for (int64_t it = item_first[h]; it < item_first[h + 1]; it++) {
+            item_col[it] = j;
+            item_slab[it] = t0 + (int)(it - item_first[h]);
+        }
+    }
+}
+
+// split[q*(T+1) + t] = offset in A~ column q of its first row >= t*R.
+__global__ void k_split(const int64_t *At_colptr, const int32_t *At_row, int64_t nq, int T, int R,
+                        int32_t *split) {
+    int64_t total = nq * (int64_t)(T + 1);
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = x / (T + 1);
+        int t = (int)(x % (T + 1));
+        int64_t s = At_colptr[q], e = At_colptr[q + 1];
+        long long bound = (long long)t * R;
+        int64_t lo = s, hi = e;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if ((long long)At_row[mid] < bound)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        split[x] = (int32_t)(lo - s);
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+static bool valid_type(int32_t v, int maxv) { return v >= 0 && v <= maxv; }
+
+static spg_status check_csc(const spg_csc *M, const char *name) {
+    if (!M) {
+        set_error("%s is NULL", name);
+        return SPG_INVALID_ARGUMENT;
+    }
+    if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0 || !valid_type(M->ptr_type, 1) ||
+        !valid_type(M->idx_type, 1) || !valid_type(M->val_type, 2)) {
+        set_error("%s: negative size or unknown type code", name);
+        return SPG_INVALID_ARGUMENT;
+    }
+    if (!M->colptr || (M->nnz > 0 && (!M->rowidx || !M->vals))) {
+        set_error("%s: missing array pointer", name);
+        return SPG_INVALID_ARGUMENT;
+    }
+    if (M->ptr_type == SPG_IDX_I32 && M->nnz > INT32_MAX) {
+        set_error("%s: nnz does not fit its int32 column pointers", name);
+        return SPG_INVALID_ARGUMENT;
+    }
+    return SPG_OK;
+}
+
+#define TRY(x)                        \
+    do {                              \
+        spg_status _s = (x);          \
+        if (_s != SPG_OK) return _s;  \
+    } while (0)
+#define LAUNCH_OK(what) TRY(cuda_check(cudaGetLastError(), what))
+
+static spg_status plan_build(spg_plan *p) {
+    const spg_csc &A = p->A, &B = p->B;
+    cudaStream_t st = p->st;
+    const int64_t m = p->m, k = p->k, n = p->n;
+    const int P = p->P;
+    const int sm = p->sm_count;
+    const int p64A = A.ptr_type == SPG_IDX_I64, i64A = A.idx_type == SPG_IDX_I64;
+    const int p64B = B.ptr_type == SPG_IDX_I64, i64B = B.idx_type == SPG_IDX_I64;
+    const size_t accsz = 8;
+
+    p->d_err = (int *)ws_alloc(p, sizeof(int) * 4);
+    p->d_cnt = (int64_t *)ws_alloc(p, sizeof(int64_t) * kCntSlots);
+    p->d_bincur = (int64_t *)ws_alloc(p, sizeof(int64_t) * kNumBins);
+    if (!p->d_err || !p->d_cnt || !p->d_bincur) return SPG_OUT_OF_MEMORY;
+    TRY(cuda_check(cudaMemsetAsync(p->d_err, 0, sizeof(int) * 4, st), "memset"));
+    TRY(cuda_check(cudaMemsetAsync(p->d_cnt, 0, sizeof(int64_t) * kCntSlots, st), "memset"));
+    cudaEventRecord(p->ev[0], st);
+
+    if (p->opt.validate) {
+        k_validate<<<grid_for(A.ncols * 32, 256, sm * 16), 256, 0, st>>>(A.colptr, p64A, A.rowidx, i64A, A.nrows,
+                                                                          A.ncols, A.nnz, p->d_err);
+        k_validate<<<grid_for(B.ncols * 32, 256, sm * 16), 256, 0, st>>>(B.colptr, p64B, B.rowidx, i64B, B.nrows,
+                                                                          B.ncols, B.nnz, p->d_err);
+        LAUNCH_OK("validate");
+        TRY(read_dev_err(p, "input validation"));
+    }
+
+    // --- step 1: D and H_i
+    p->W = (k + 31) / 32;
+    const int64_t W = p->W;
+    p->Dbits = (uint32_t *)ws_alloc(p, sizeof(uint32_t) * (size_t)(W + 1));
+    p->Hbits = (uint32_t *)ws_alloc(p, sizeof(uint32_t) * (size_t)(P * W + 1));
+    p->rankpre = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(P * W + 1));
+    int32_t *popc = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(P * W + 1));
+    p->nfb = (k + p->b - 1) / p->b;
+    p->fetch = (uint8_t *)ws_alloc(p, (size_t)(P * p->nfb + 1));
+    if (!p->Dbits || !p->Hbits || !p->rankpre || !popc || !p->fetch) return SPG_OUT_OF_MEMORY;
+    TRY(cuda_check(cudaMemsetAsync(p->Hbits, 0, sizeof(uint32_t) * (size_t)(P * W + 1), st), "memset H"));
+    if (W > 0) k_nonempty_bits<<<grid_for(W, 256, sm * 8), 256, 0, st>>>(A.colptr, p64A, k, W, p->Dbits);
+    if (n > 0) k_mark_H<<<grid_for(n * 32, 256, sm * 16), 256, 0, st>>>(B.colptr, p64B, B.rowidx, i64B, n, P, W, p->Hbits);
+    LAUNCH_OK("mark H");
+
+    // --- step 2: D~_i = H_i & D, its ranks and Algorithm 2
+    int64_t PW = (int64_t)P * W;
+    if (PW > 0)
+        k_popc_HD<<<grid_for(PW, 256, sm * 8), 256, 0, st>>>(p->Hbits, p->Dbits, W, PW, popc,
+                                                            (long long *)(p->d_cnt + kCntSumH));
+    TRY(scan_exclusive_i32(p, popc, p->rankpre, PW));
+    // |D~| in total and per block: read the block boundaries of the scan
+    std::vector<int64_t> idx(P + 1);
+    for (int i = 0; i <= P; i++) idx[i] = (int64_t)i * W;
+    for (int i = 0; i <= P; i++)
+        TRY(cuda_check(cudaMemcpyAsync(p->h_pinned + i, p->rankpre + idx[i], sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+                       "rank readback"));
+    TRY(cuda_check(cudaStreamSynchronize(st), "rank readback"));
+    p->dt_base.assign(p->h_pinned, p->h_pinned + P + 1);
+    p->ndt = p->dt_base[P];
+    if (p->ndt >= INT32_MAX) {
+        set_error("sum of |D~_i| (%lld) exceeds int32", (long long)p->ndt);
+        return SPG_UNSUPPORTED;
+    }
+    p->dtilde = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->ndt + 1));
+    p->At_colptr = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->ndt + 1));
+    int64_t *glen = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->ndt + 1));
+    if (!p->dtilde || !p->At_colptr || !glen) return SPG_OUT_OF_MEMORY;
+    if (PW > 0) k_dtilde<<<grid_for(PW, 256, sm * 8), 256, 0, st>>>(p->Hbits, p->Dbits, p->rankpre, W, PW, p->dtilde);
+    if (P * p->nfb > 0)
+        k_fetch<<<grid_for(P * p->nfb, 256, sm * 8), 256, 0, st>>>(
+            p->Hbits, p->Dbits, p->rankpre, W, k, p->b, p->nfb, P, A.colptr, p64A, p->fetch,
+            (long long *)(p->d_cnt + kCntFetchChosen), (long long *)(p->d_cnt + kCntVolBlock));
+    LAUNCH_OK("dtilde / fetch");
+
+    // --- step 3: gather A~
+    if (p->ndt > 0)
+        k_gather_len<<<grid_for(p->ndt, 256, sm * 8), 256, 0, st>>>(p->dtilde, p->ndt, A.colptr, p64A, glen,
+                                                                  (long long *)(p->d_cnt + kCntMaxAcol));
+    TRY(scan_exclusive_i64(p, glen, p->At_colptr, p->ndt));
+    TRY(cuda_check(cudaMemcpyAsync(p->h_pinned, p->At_colptr + p->ndt, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "readback"));
+    TRY(cuda_check(cudaMemcpyAsync(p->h_pinned + 1, p->d_cnt + kCntMaxAcol, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "readback"));
+    TRY(cuda_check(cudaStreamSynchronize(st), "readback"));
+    p->nAt = p->h_pinned[0];
+    if (p->h_pinned[1] >= (1LL << 26)) {
+        set_error("a column of A holds %lld nonzeros; this build supports < 2^26 per column", (long long)p->h_pinned[1]);
+        return SPG_UNSUPPORTED;
+    }
+    p->At_row = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->nAt + 1));
+    p->At_val = ws_alloc(p, accsz * (size_t)(p->nAt + 1));
+    p->Bq = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->nnzB + 1));
+    p->Bv = ws_alloc(p, accsz * (size_t)(p->nnzB + 1));
+    if (!p->At_row || !p->At_val || !p->Bq || !p->Bv) return SPG_OUT_OF_MEMORY;
+    if (P * p->nfb > 0 && p->nAt > 0) {
+        int g = grid_for(P * p->nfb, 1, sm * 8);
+        if (p->acc_f64)
+            k_gather_copy<double><<<g, 256, 0, st>>>(p->Hbits, p->Dbits, p->rankpre, W, k, p->b, p->nfb, P, p->fetch,
+                                                     p->dtilde, A.colptr, p64A, A.rowidx, i64A, A.vals, A.val_type,
+                                                     p->At_colptr, p->At_row, (double *)p->At_val);
+        else
+            k_gather_copy<long long><<<g, 256, 0, st>>>(p->Hbits, p->Dbits, p->rankpre, W, k, p->b, p->nfb, P,
+                                                        p->fetch, p->dtilde, A.colptr, p64A, A.rowidx, i64A, A.vals,
+                                                        A.val_type, p->At_colptr, p->At_row, (long long *)p->At_val);
+        LAUNCH_OK("gather");
+    }
+    if (n > 0) {
+        int g = grid_for(n * 32, 256, sm * 16);
+        if (p->acc_f64)
+            k_remap_B<double><<<g, 256, 0, st>>>(B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P, p->Hbits,
+                                                 p->Dbits, p->rankpre, W, p->Bq, (double *)p->Bv);
+        else
+            k_remap_B<long long><<<g, 256, 0, st>>>(B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P,
+                                                    p->Hbits, p->Dbits, p->rankpre, W, p->Bq, (long long *)p->Bv);
+        LAUNCH_OK("remap B");
+    }
+
+    // --- step 4: flops, windows, bins
+    p->flops = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(n + 1));
+    p->win_lo = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(n + 1));
+    p->win_hi = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(n + 1));
+    p->nnzb = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(n + 1));
+    p->maxa = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(n + 1));
+    p->bin_of = (int8_t *)ws_alloc(p, (size_t)(n + 1));
+    p->binlist = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(n + 1));
+    p->nnzcol = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(n + 1));
+    p->Ccolptr = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(n + 1));
+    if (!p->flops || !p->win_lo || !p->win_hi || !p->nnzb || !p->maxa || !p->bin_of || !p->binlist ||
+        !p->nnzcol || !p->Ccolptr)
+        return SPG_OUT_OF_MEMORY;
+    if (n > 0) {
+        k_col_stats<<<grid_for(n * 32, 256, sm * 16), 256, 0, st>>>(
+            B.colptr, p64B, n, p->Bq, p->At_colptr, p->At_row, p->light_max, p->flops, p->win_lo, p->win_hi,
+            p->nnzb, p->maxa, p->bin_of, (long long *)(p->d_cnt + kCntBin0), (long long *)(p->d_cnt + kCntProducts));
+        LAUNCH_OK("column stats");
+        TRY(bin_columns(p, p->bin_of, p->binlist, p->bin_off));
+    }
+    p->nheavy = p->bin_off[kBinHeavy + 1] - p->bin_off[kBinHeavy];
+
+    // --- heavy bins: slab items and the split index of A~
+    p->T = (int)((m + p->R - 1) / p->R);
+    if (p->T < 1) p->T = 1;
+    if (p->nheavy > 0) {
+        const int32_t *hl = p->binlist + p->bin_off[kBinHeavy];
+        int64_t *nslab = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
+        p->item_first = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
+        if (!nslab || !p->item_first) return SPG_OUT_OF_MEMORY;
+        k_heavy_nslab<<<grid_for(p->nheavy, 256, sm * 8), 256, 0, st>>>(hl, p->nheavy, p->win_lo, p->win_hi, p->R, nslab);
+        TRY(scan_exclusive_i64(p, nslab, p->item_first, p->nheavy));
+        TRY(cuda_check(cudaMemcpyAsync(p->h_pinned, p->item_first + p->nheavy, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "items"));
+        TRY(cuda_check(cudaStreamSynchronize(st), "items"));
+        p->nitems = p->h_pinned[0];
+        p->item_col = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nitems);
+        p->item_slab = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nitems);
+        p->item_cnt = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nitems);
+        p->item_off = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)p->nitems);
+        p->hbits = (uint32_t *)ws_alloc(p, sizeof(uint32_t) * (size_t)p->nitems * (size_t)(p->R / 32));
+        p->split = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->ndt + 1) * (size_t)(p->T + 1));
+        if (!p->item_col || !p->item_slab || !p->item_cnt || !p->item_off || !p->hbits || !p->split)
+            return SPG_OUT_OF_MEMORY;
+        k_heavy_items<<<grid_for(p->nheavy, 256, sm * 8), 256, 0, st>>>(hl, p->nheavy, p->win_lo, p->R, p->item_first,
+                                                                        p->item_col, p->item_slab);
+        if (p->ndt > 0)
+            k_split<<<grid_for(p->ndt * (p->T + 1), 256, sm * 16), 256, 0, st>>>(p->At_colptr, p->At_row, p->ndt, p->T,
+                                                                                 p->R, p->split);
+        LAUNCH_OK("heavy items");
+    }
+    cudaEventRecord(p->ev[1], st);
+
+    // statistics
+    TRY(cuda_check(cudaMemcpyAsync(p->h_pinned, p->d_cnt, sizeof(int64_t) * kCntSlots, cudaMemcpyDeviceToHost, st), "stats"));
+    TRY(cuda_check(cudaStreamSynchronize(st), "stats"));
+    spg_stats &S = p->stats;
+    S.m = m; S.k = k; S.n = n; S.nnzA = p->nnzA; S.nnzB = p->nnzB; S.P = P; S.b = p->b;
+    S.products = p->h_pinned[kCntProducts];
+    S.nnzC = -1;
+    S.sum_H = p->h_pinned[kCntSumH];
+    S.sum_dtilde = p->ndt;
+    S.fetch_blocks_total = (int64_t)P * p->nfb;
+    S.fetch_blocks_chosen = p->h_pinned[kCntFetchChosen];
+    S.gathered_nnz_exact = p->nAt;
+    S.gathered_nnz_block = p->h_pinned[kCntVolBlock];
+    S.empty_columns = p->bin_off[kBinEmpty + 1] - p->bin_off[kBinEmpty];
+    S.heavy_columns = p->nheavy;
+    S.light_columns = n - S.empty_columns - S.heavy_columns;
+    S.heavy_items = p->nitems;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]);
+    S.ms_plan = ms;
+    return read_dev_err(p, "plan");
+}
+
+}  // namespace spg
+
+using namespace spg;
+
+extern "C" void spgemm_default_options(spg_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->P = 1;
+    opt->b = 1024;
+    opt->sizing = SPG_SIZING_EXACT;
+    opt->validate = 1;
+    opt->learned_slack = 1.25;
+}
+
+extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_plan **out) {
+    clear_error();
+    if (!out) {
+        set_error("out is NULL");
+        return SPG_INVALID_ARGUMENT;
+    }
+    *out = nullptr;
+    if (!opt) {
+        set_error("options are NULL");
+        return SPG_INVALID_ARGUMENT;
+    }
+    TRY(check_csc(A, "A"));
+    TRY(check_csc(B, "B"));
+    if (A->ncols != B->nrows) {
+        set_error("dimension mismatch: A is %lld x %lld, B is %lld x %lld", (long long)A->nrows, (long long)A->ncols,
+                  (long long)B->nrows, (long long)B->ncols);
+        return SPG_INVALID_ARGUMENT;
+    }
+    bool fa = A->val_type == SPG_VAL_F64, fb = B->val_type == SPG_VAL_F64;
+    if (fa != fb) {
+        set_error("A and B must both hold doubles or both hold integers");
+        return SPG_INVALID_ARGUMENT;
+    }
+    if (A->idx_type != B->idx_type) {
+        set_error("A and B must use the same row index type");
+        return SPG_INVALID_ARGUMENT;
+    }
+    if (opt->P < 1 || opt->b < 1) {
+        set_error("P and b must be >= 1 (P=%d, b=%lld)", opt->P, (long long)opt->b);
+        return SPG_INVALID_ARGUMENT;
+    }
+    if (opt->sizing != SPG_SIZING_EXACT && opt->sizing != SPG_SIZING_LEARNED) {
+        set_error("unknown sizing mode %d", opt->sizing);
+        return SPG_INVALID_ARGUMENT;
+    }
+    if (A->nrows >= INT32_MAX || A->ncols >= INT32_MAX || B->ncols >= INT32_MAX) {
+        set_error("m, k and n must be < 2^31 - 1");
+        return SPG_UNSUPPORTED;
+    }
+    int lm = opt->light_max ? opt->light_max : 1024;
+    int R = opt->slab_rows ? opt->slab_rows : 8192;
+    if (lm < 32 || lm > 1024 || (lm & (lm - 1)) || R < 1024 || R > 16384 || (R & (R - 1))) {
+        set_error("light_max must be a power of two in [32, 1024] and slab_rows one in [1024, 16384]");
+        return SPG_INVALID_ARGUMENT;
+    }
+
+    spg_plan *p = new (std::nothrow) spg_plan();
+    if (!p) {
+        set_error("host allocation failed");
+        return SPG_OUT_OF_MEMORY;
+    }
+    p->A = *A;
+    p->B = *B;
+    p->opt = *opt;
+    p->st = (cudaStream_t)opt->stream;
+    p->m = A->nrows;
+    p->k = A->ncols;
+    p->n = B->ncols;
+    p->nnzA = A->nnz;
+    p->nnzB = B->nnz;
+    p->P = opt->P;
+    p->b = opt->b;
+    p->acc_f64 = fa;
+    p->out_idx64 = A->idx_type == SPG_IDX_I64;
+    p->light_max = lm;
+    p->R = R;
+    int dev = 0;
+    spg_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (!s) s = cuda_check(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev), "attr");
+    if (!s) s = cuda_check(cudaMallocHost(&p->h_pinned, sizeof(int64_t) * 64), "cudaMallocHost");
+    for (int i = 0; i < 8 && !s; i++) s = cuda_check(cudaEventCreate(&p->ev[i]), "event");
+    if (!s) s = plan_build(p);
+    if (s) {
+        std::string keep = last_error_str();
+        spgemm_plan_destroy(p);
+        set_error("%s", keep.c_str());
+        return s;
+    }
+    *out = p;
+    return SPG_OK;
+}
+
+extern "C" spg_status spgemm_plan_destroy(spg_plan *p) {
+    if (!p) return SPG_OK;
+    ws_free_all(p);
+    cudaStreamSynchronize(p->st);
+    for (int i = 0; i < 8; i++)
+        if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    if (p->h_pinned) cudaFreeHost(p->h_pinned);
+    delete p;
+    return SPG_OK;
+}

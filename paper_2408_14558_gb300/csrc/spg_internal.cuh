@@ -1,0 +1,258 @@
+// Internal declarations of the GB300 sparsity-aware 1D SpGEMM library.
+//
+// Layout in HBM (all per plan, all P column blocks processed together):
+//   Dbits     ceil(k/32) u32          nonempty columns of A (the set D of Algorithm 1)
+//   Hbits     P * W u32               H_i, nonzero rows of B_i (Table 1), W = ceil(k/32)
+//   rankpre   P * W + 1 i64           exclusive prefix of popc(H_i & D) over (block, word):
+//                                     the global index of the first required column of a word
+//   dtilde    sum|D~_i| i32           required column ids, block after block, ascending
+//   fetch     P * ceil(k/b) u8        chosen fetch blocks (Algorithm 2)
+//   At_*      CSC of all A~_i         colptr i64 (sum|D~_i| + 1), rows i32, values Acc
+//   Bq, Bv    nnz(B) i32 / Acc        B with each row k replaced by its column of A~_i (-1 if
+//                                     column k of A is empty), values widened to Acc
+//   flops, win_lo/hi, nnzb, maxa      per output column statistics (Section 3.2 flop count)
+//   binlist   n i32                   column ids grouped by bin
+//   split     sum|D~_i| * (T+1) i32   heavy bins only: offset of the first row >= t*R in each
+//                                     A~ column (R rows per slab, T = ceil(m/R))
+//   hbits     items * R/32 u32        heavy bins only: symbolic row bitmap of each (column, slab)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "spgemm1d.h"
+
+namespace spg {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kEmptyKey = -1;
+
+// Per-column bins.  0: no products.  1..6: warp hash with table size 32 << bin.
+// 7: dense row slabs (heavy).
+constexpr int kBinEmpty = 0;
+constexpr int kBinHeavy = 7;
+constexpr int kNumBins = 8;
+constexpr int kMaxLightBin = 6;
+
+// Device error bits (OR-ed into plan->d_err).
+enum : int {
+    kDevErrInput = 1,      // input not canonical
+    kDevErrInternal = 2,   // a kernel found an inconsistency (hash full, count mismatch)
+    kDevErrRange = 4,      // a size limit of this build was exceeded
+};
+
+struct Alloc {
+    void *p;
+    size_t bytes;
+};
+
+}  // namespace spg
+
+struct spg_plan {
+    spg_csc A{}, B{};
+    spg_options opt{};
+    cudaStream_t st = nullptr;
+    int64_t m = 0, k = 0, n = 0, nnzA = 0, nnzB = 0;
+    int P = 1;
+    int64_t b = 1;
+    bool acc_f64 = true;     // double accumulation, else int64 wrapping
+    bool out_idx64 = false;  // C row ids int64
+    int64_t W = 0;           // u32 words per H_i bitmap
+    int64_t nfb = 0;         // fetch blocks per column block
+    int light_max = 1024;
+    int R = 8192, T = 1;     // heavy slab rows and slab count
+    int sm_count = 0;
+
+    std::vector<spg::Alloc> allocs;
+    int *d_err = nullptr;
+    int64_t *d_cnt = nullptr;      // small device counters (see kCnt* in plan.cu)
+    int64_t *h_pinned = nullptr;   // pinned host mirror for read-backs
+
+    uint32_t *Dbits = nullptr, *Hbits = nullptr;
+    int64_t *rankpre = nullptr;
+    int32_t *dtilde = nullptr;
+    int64_t ndt = 0;
+    std::vector<int64_t> dt_base;  // host: first global D~ index of each block (P + 1)
+    uint8_t *fetch = nullptr;
+    int64_t *At_colptr = nullptr;
+    int32_t *At_row = nullptr;
+    void *At_val = nullptr;
+    int64_t nAt = 0;
+    int32_t *Bq = nullptr;
+    void *Bv = nullptr;
+    int64_t *flops = nullptr;
+    int32_t *win_lo = nullptr, *win_hi = nullptr, *nnzb = nullptr, *maxa = nullptr;
+    int8_t *bin_of = nullptr;
+    int32_t *binlist = nullptr;
+    int64_t bin_off[spg::kNumBins + 1] = {0};
+    int64_t *d_bincur = nullptr;
+
+    // heavy bins
+    int64_t nheavy = 0, nitems = 0;
+    int32_t *split = nullptr;
+    int64_t *item_first = nullptr;  // per heavy column: first item (nheavy + 1)
+    int32_t *item_col = nullptr, *item_slab = nullptr;
+    int32_t *item_cnt = nullptr;
+    int64_t *item_off = nullptr;
+    uint32_t *hbits = nullptr;
+
+    // symbolic / numeric
+    int64_t *nnzcol = nullptr;
+    int64_t *Ccolptr = nullptr;  // plan-owned copy of C's column pointers
+    int64_t nnzC = -1;
+    bool symbolic_done = false;
+    int32_t *nbinlist = nullptr;
+    int64_t nbin_off[spg::kNumBins + 1] = {0};
+
+    spg_stats stats{};
+    cudaEvent_t ev[8] = {nullptr};
+};
+
+namespace spg {
+
+// ---- host helpers (plan.cu)
+void set_error(const char *fmt, ...);
+spg_status cuda_check(cudaError_t e, const char *what);
+void *ws_alloc(spg_plan *p, size_t bytes);
+void ws_free_all(spg_plan *p);
+spg_status read_dev_err(spg_plan *p, const char *phase);
+int grid_for(int64_t work, int per_block, int max_blocks);
+
+// ---- scans (scan.cu): out[0..n] = exclusive prefix of in[0..n), out[n] = total.
+spg_status scan_exclusive_i32(spg_plan *p, const int32_t *in, int64_t *out, int64_t n);
+spg_status scan_exclusive_i64(spg_plan *p, const int64_t *in, int64_t *out, int64_t n);
+
+// ---- binning (plan.cu): group the columns whose bin id is in bin_of into binlist.
+spg_status bin_columns(spg_plan *p, const int8_t *bin_of, int32_t *list, int64_t *off_host);
+
+// ---- phases
+spg_status run_symbolic(spg_plan *p);
+spg_status run_numeric(spg_plan *p, spg_csc *C);
+
+// ---- device helpers
+__device__ __forceinline__ int64_t ld_ptr(const void *p, int is64, int64_t i) {
+    return is64 ? (int64_t)__ldg((const long long *)p + i) : (int64_t)__ldg((const int *)p + i);
+}
+
+// Column block of output column j: block i holds [floor(i*n/P), floor((i+1)*n/P)).
+__device__ __forceinline__ int block_of(int64_t j, int64_t n, int P) {
+    return (int)(((j + 1) * (int64_t)P - 1) / n);
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc mul_acc(Acc a, Acc b);
+template <>
+__device__ __forceinline__ double mul_acc<double>(double a, double b) { return a * b; }
+template <>
+__device__ __forceinline__ long long mul_acc<long long>(long long a, long long b) {
+    return (long long)((unsigned long long)a * (unsigned long long)b);
+}
+
+__device__ __forceinline__ void atomic_add_acc(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_acc(long long *p, long long v) {
+    atomicAdd((unsigned long long *)p, (unsigned long long)v);
+}
+
+// Per-warp scratch for walking the products of one output column.
+template <typename Acc>
+struct WarpSeg {
+    int pref[33];
+    long long start[32];
+    Acc bv[32];
+};
+
+// Walk every product of the B' entries [p0, p1) of one output column with a
+// whole warp.  seg(p, start, len, bv) gives the A~ positions [start, start+len)
+// that B' entry p multiplies and its value.  The lengths of 32 consecutive
+// entries are prefix-summed so that all 32 lanes stay busy however short the
+// segments are; body(row, product) is called once per product.
+template <bool NEED_VAL, typename Acc, typename SegFn, typename Body>
+__device__ __forceinline__ void warp_products(int64_t p0, int64_t p1, int lane, WarpSeg<Acc> &ws,
+                                              const int32_t *__restrict__ At_row,
+                                              const Acc *__restrict__ At_val, SegFn seg, Body body) {
+    for (int64_t base = p0; base < p1; base += 32) {
+        int64_t p = base + lane;
+        long long st = 0;
+        int len = 0;
+        Acc bv = Acc(0);
+        if (p < p1) seg(p, st, len, bv);
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int total = __shfl_sync(kFull, incl, 31);
+        ws.pref[lane] = incl - len;
+        ws.start[lane] = st;
+        if (NEED_VAL) ws.bv[lane] = bv;
+        __syncwarp();
+        for (int f0 = 0; f0 < total; f0 += 32) {
+            int fi = f0 + lane;
+            if (fi < total) {
+                int s = 0;
+#pragma unroll
+                for (int stp = 16; stp > 0; stp >>= 1)
+                    if (ws.pref[s + stp] <= fi) s += stp;
+                long long e = ws.start[s] + (fi - ws.pref[s]);
+                int r = __ldg(At_row + e);
+                if (NEED_VAL)
+                    body(r, mul_acc<Acc>(__ldg(At_val + e), ws.bv[s]));
+                else
+                    body(r, Acc(0));
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ unsigned hash_row(int r, int shift) {
+    return ((unsigned)r * 0x9E3779B1u) >> shift;
+}
+
+// Insert row r into an open-addressing table of 2^logS int keys (linear
+// probing).  Returns the slot, and sets *fresh when this call created it.
+// The table is sized >= 2x its final occupancy, so a free slot is always
+// reached; the probe count is still bounded (-1 = table full).
+__device__ __forceinline__ int hash_insert(int *keys, int logS, int r, bool *fresh) {
+    const int mask = (1 << logS) - 1;
+    unsigned h = hash_row(r, 32 - logS);
+    volatile int *vk = keys;
+    for (int probe = 0; probe <= mask; probe++) {
+        int cur = vk[h];
+        if (cur == r) {
+            *fresh = false;
+            return (int)h;
+        }
+        if (cur == kEmptyKey) {
+            int old = atomicCAS(keys + h, kEmptyKey, r);
+            if (old == kEmptyKey) {
+                *fresh = true;
+                return (int)h;
+            }
+            if (old == r) {
+                *fresh = false;
+                return (int)h;
+            }
+        }
+        h = (h + 1) & mask;
+    }
+    *fresh = false;
+    return -1;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+}  // namespace spg

@@ -1,0 +1,91 @@
+"""Host-side checks of the C ABI boundary (no GPU needed): the shared library
+builds for sm_103a, loads, exports every function include/spgemm1d.h declares,
+and the ctypes structures of the binding have the C layout."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "spgemm1d.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2408_14558_gb300 import build
+    build.build()
+    import paper_2408_14558_gb300 as g
+    return g.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(spgemm_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("spgemm_plan", "spgemm_symbolic", "spgemm_numeric", "spgemm_1d_multiply",
+                     "spgemm_plan_stats", "spgemm_plan_destroy", "spgemm_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts_match_header(tmp_path):
+    import paper_2408_14558_gb300 as g
+    prog = tmp_path / "layout.c"
+    prog.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "spgemm1d.h"
+int main(void) {
+  printf("%zu %zu %zu\\n", sizeof(spg_csc), sizeof(spg_options), sizeof(spg_stats));
+  printf("%zu %zu %zu %zu\\n", offsetof(spg_csc, colptr), offsetof(spg_options, stream),
+         offsetof(spg_options, learned_slack), offsetof(spg_stats, ms_plan));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split()
+    sizes = list(map(int, out))
+    assert sizes[0] == ctypes.sizeof(g.spg_csc)
+    assert sizes[1] == ctypes.sizeof(g.spg_options)
+    assert sizes[2] == ctypes.sizeof(g.spg_stats)
+    assert sizes[3] == g.spg_csc.colptr.offset
+    assert sizes[4] == g.spg_options.stream.offset
+    assert sizes[5] == g.spg_options.learned_slack.offset
+    assert sizes[6] == g.spg_stats.ms_plan.offset
+
+
+def test_default_options(lib):
+    import paper_2408_14558_gb300 as g
+    o = g.spg_options()
+    lib.spgemm_default_options(ctypes.byref(o))
+    assert (o.P, o.b, o.validate, o.sizing) == (1, 1024, 1, g.SPG_SIZING_EXACT)
+
+
+def test_argument_errors_need_no_gpu(lib):
+    """Argument checks run before any CUDA call."""
+    import paper_2408_14558_gb300 as g
+    A = g.spg_csc(4, 5, 0, 0, 0, 0, 0, 1, None, None)
+    B = g.spg_csc(6, 3, 0, 0, 0, 0, 0, 1, None, None)      # 5 != 6
+    o = g.spg_options()
+    lib.spgemm_default_options(ctypes.byref(o))
+    h = ctypes.c_void_p()
+    assert lib.spgemm_plan(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(h)) == g.SPG_INVALID_ARGUMENT
+    assert "dimension mismatch" in g.spgemm_last_error()
+    B.nrows = 5
+    o.P = 0
+    assert lib.spgemm_plan(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(h)) == g.SPG_INVALID_ARGUMENT
+    o.P = 2
+    B.val_type = g.SPG_VAL_I64
+    assert lib.spgemm_plan(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(h)) == g.SPG_INVALID_ARGUMENT
+    assert not h.value
