@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 sparsity-aware 1D SpGEMM; prints one JSON line.
+
+Workload (the paper's squaring use case, Section 4.1, on a synthetic stand-in
+for its SuiteSparse graphs): R-MAT scale 18 (262,144 vertices), edge factor 16,
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), self-loops dropped, duplicates merged,
+symmetrised; C = A * A with P = 16 column blocks and fetch blocks of b = 1024
+column ids.  One step runs it twice: double values 1.0 and the int64 (+, x)
+path-count semiring.  GFLOP = 2 x products.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Timing: inputs resident in HBM; each timed step is bracketed by CUDA events on
+the library's stream and preceded (outside the timed region) by a 256 MiB write
+that evicts L2.  Under torchrun every rank runs the whole workload on its own
+GPU (weak scaling), the step times are maxed over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "C=A·B GFLOP/s & % HBM roofline; learned/batched vs plain GPU time, exact C"
+WORKLOAD = "rmat_s18_ef16_symmetric_squaring"
+P_BLOCKS, FETCH_B = 16, 1024
+CPU_SAMPLE_COLS = 65536      # columns of C computed by the oracle for the CPU baseline
+REF_SAMPLE_COLS = 16384      # per step of the reference arm
+FLUSH_BYTES = 256 << 20      # > 2 x the 126 MiB L2
+BYTES_PER_NZ = 12            # int32 row id + 8-byte value
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_workload():
+    import synth
+    A = synth.rmat_symmetric(18, 16, seed=0)
+    Ai = synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.vals.astype(np.int64))
+    return A, Ai
+
+
+def workload_config(products_per_run, nnzC):
+    return {"workload": WORKLOAD, "P": P_BLOCKS, "b": FETCH_B,
+            "runs_per_step": ["f64 values 1.0", "int64 path counts"],
+            "n": 1 << 18, "nnzA": None, "products_per_run": products_per_run, "nnzC_per_run": nnzC,
+            "index_types": "int32 colptr / int32 row ids", "l2": "flushed before every timed step (256 MiB write)"}
+
+
+# --------------------------------------------------------------- aggregation
+
+def aggregate(local_ms: float, local_flop: float, world: int):
+    """Max step time over ranks and the flops of all ranks (weak scaling)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        f = torch.tensor([local_flop], dtype=torch.float64, device=dev)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+        return float(t.item()), float(f.item())
+    return local_ms, local_flop
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def time_oracle(A, ncols_sample: int, seed: int):
+    import oracle
+    rng = np.random.default_rng(seed)
+    cols = np.sort(rng.choice(A.ncols, ncols_sample, replace=False))
+    t0 = time.perf_counter()
+    r = oracle.spgemm(A, A, cols=cols)
+    dt = time.perf_counter() - t0
+    products = int(r["flops"].sum())
+    return {"value": 2.0 * products / dt / 1e9, "unit": "GFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{ncols_sample} random output columns (seed {seed}) of the f64 run: {products} products, "
+                      f"{dt:.2f} s", "seconds": dt, "products": products}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    A, _ = make_workload()
+    for w in range(args.warmup):
+        time_oracle(A, REF_SAMPLE_COLS, seed=100 + w)
+    secs, prods = [], []
+    for s in range(args.steps):
+        r = time_oracle(A, REF_SAMPLE_COLS, seed=s)
+        secs.append(r["seconds"])
+        prods.append(r["products"])
+    import oracle
+    val = 2.0 * sum(prods) / sum(secs) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(None, None),
+            "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"each step: {REF_SAMPLE_COLS} random output columns of the f64 run"},
+            "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- roofline
+
+def _source_digest():
+    h = hashlib.sha256()
+    for name in ("numeric.cu", "symbolic.cu", "spg_internal.cuh", "plan.cu"):
+        with open(os.path.join(ROOT, "paper_2408_14558_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    if there is none or the sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_rmat_s18.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    d = re.search(r"source_digest:\s*([0-9a-f]+)", txt)
+    if not m or not d or d.group(1) != _source_digest():
+        return None
+    return float(m.group(1))
+
+
+def kernel_bytes(group: str, st: dict) -> float:
+    """Algorithmic bytes of one launch group of one run:
+    numeric heavy: write its C entries, read its B entries and A~ once;
+    numeric light: the same for the light columns; symbolic: read B rows and
+    A~ rows once, write one count per column; gather: read and write A~."""
+    nzc_h = max(st["nnzC_heavy"], 0)
+    if group == "num_heavy":
+        return (BYTES_PER_NZ * (nzc_h + st["nnzB_heavy"] + st["gathered_nnz_exact"]) + 8 * st["heavy_columns"])
+    if group == "num_light":
+        return (BYTES_PER_NZ * (st["nnzC"] - nzc_h + st["nnzB"] - st["nnzB_heavy"] + st["gathered_nnz_exact"])
+                + 8 * st["light_columns"])
+    if group == "sym_heavy":
+        return 4 * (st["nnzB_heavy"] + st["gathered_nnz_exact"]) + 8 * st["heavy_columns"]
+    if group == "sym_light":
+        return 4 * (st["nnzB"] - st["nnzB_heavy"] + st["gathered_nnz_exact"]) + 8 * st["light_columns"]
+    if group == "gather":
+        return 2 * BYTES_PER_NZ * st["gathered_nnz_exact"]
+    return 0.0
+
+
+def compulsory_bytes(st: dict) -> float:
+    """B (colptr + rows + values) + gathered A once + C (rows + values + int64 colptr)."""
+    return (4 * (st["n"] + 1) + BYTES_PER_NZ * st["nnzB"] + BYTES_PER_NZ * st["gathered_nnz_exact"]
+            + 8 * st["sum_dtilde"] + BYTES_PER_NZ * st["nnzC"] + 8 * (st["n"] + 1))
+
+
+def measured_peak_hbm():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------- main
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_2408_14558_gb300 as g
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.load_library()
+    A, Ai = make_workload()
+    dA = g.to_device(A, ptr_dtype=torch.int32, idx_dtype=torch.int32)
+    dAi = g.to_device(Ai, ptr_dtype=torch.int32, idx_dtype=torch.int32)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        sts = []
+        for X in (dA, dAi):
+            plan = g.spgemm_plan(X, X, P_BLOCKS, FETCH_B)
+            colptr, nnz = g.spgemm_symbolic(plan)
+            C = g.spgemm_numeric(plan, colptr)
+            sts.append(g.spgemm_plan_stats(plan))
+            g.spgemm_plan_destroy(plan)
+            del C, colptr
+        return sts
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, stats = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for s in range(args.steps):
+        flush.fill_(s)
+        e0.record(stream)
+        sts = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(sts)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+
+    products_step = sum(st["products"] for st in stats[0])
+    flop_local = 2.0 * products_step * args.steps
+    total_ms, flop_all = aggregate(sum(times), flop_local, world)
+    value = flop_all / (total_ms / 1e3) / 1e9
+    ms_per_step = total_ms / args.steps
+
+    # dominant kernel group and its roofline
+    groups = ["gather", "sym_light", "sym_heavy", "num_light", "num_heavy"]
+    per_group = {gname: statistics.mean(sum(st["ms_" + gname] for st in sts) for sts in stats) for gname in groups}
+    dom = max(per_group, key=per_group.get)
+    dom_bytes = sum(kernel_bytes(dom, st) for st in stats[0])        # both runs of one step
+    dom_ms = per_group[dom]
+    peak, peak_src = measured_peak_hbm()
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    kernel_name = {"num_heavy": "k_num_heavy", "num_light": "k_num_light", "sym_heavy": "k_sym_heavy",
+                   "sym_light": "k_sym_light", "gather": "k_gather_copy"}[dom]
+    comp = sum(compulsory_bytes(st) for st in stats[0])
+    path_gbs = comp / (ms_per_step / 1e3) / 1e9
+    launches = sum(st["kernel_launches"] for sts in stats for st in sts)
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+int64", "data": "synthetic",
+            "config": workload_config(stats[0][0]["products"], stats[0][0]["nnzC"]),
+            "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic(kernel_name),
+                         "algorithmic_bytes_per_step": dom_bytes, "ms_per_step": dom_ms,
+                         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
+            "path_roofline": {"compulsory_bytes_per_step": comp, "achieved": path_gbs, "frac": path_gbs / peak,
+                              "unit": "GB/s"},
+            "kernel_ms_per_step": {k: round(v, 4) for k, v in per_group.items()},
+            "phase_ms_per_step": {ph: statistics.mean(sum(st["ms_" + ph] for st in sts) for sts in stats)
+                                  for ph in ("plan", "symbolic", "numeric")},
+            "gpu_launches": launches, "clocks": clk}
+    line["config"]["nnzA"] = A.nnz
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = time_oracle(A, CPU_SAMPLE_COLS, seed=0)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(g, torch, A, Ai, max(1, min(args.steps, 3)), world, products_step)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(g, torch, A, Ai, steps, world, products_step):
+    """The same metric through the one-call C ABI with host buffers: every step
+    copies the inputs from pinned host memory, multiplies (plan, symbolic,
+    numeric, with C allocated through the callbacks) and reads all of C back
+    into pinned host memory."""
+    hosts = []
+    for M in (A, Ai):
+        hosts.append([torch.from_numpy(M.colptr.astype(np.int32)).pin_memory(),
+                      torch.from_numpy(M.rowidx.astype(np.int32)).pin_memory(),
+                      torch.from_numpy(M.vals).pin_memory()])
+    chunk = 4 << 30
+    host_out = torch.empty(chunk, dtype=torch.uint8).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for h in hosts for t in h)
+    d2h_total, secs = 0, []
+
+    def read_back(t):
+        flat = t.view(torch.uint8) if t.numel() else t
+        n = flat.numel()
+        for o in range(0, n, chunk):
+            m = min(chunk, n - o)
+            host_out[:m].copy_(flat[o:o + m], non_blocking=True)
+        return n
+
+    for s in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for (cp, ri, va), M in zip(hosts, (A, Ai)):
+            dX = g.DeviceCSC(M.nrows, M.ncols, cp.to("cuda", non_blocking=True), ri.to("cuda", non_blocking=True),
+                             va.to("cuda", non_blocking=True))
+            C, st = g.spgemm_1d_multiply(dX, dX, P=P_BLOCKS, b=FETCH_B)
+            for t in (C.colptr, C.rowidx, C.vals):
+                d2h += read_back(t)
+            del C, dX
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if s > 0:                       # the first pass warms the allocator
+            secs.append(dt)
+            d2h_total = d2h
+    local_s = statistics.mean(secs)
+    t_all, flop_all = aggregate(local_s, 2.0 * products_step, world)
+    return {"value": flop_all / t_all / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h_total, "steps": len(secs), "ms_per_step": 1e3 * t_all,
+            "timing": "wall clock, synchronize on both sides of each step"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

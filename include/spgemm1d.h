@@ -113,7 +113,13 @@ typedef struct {
     int64_t gathered_nnz_block;  /* nonzeros inside the chosen fetch blocks (block-granular volume) */
     int64_t light_columns, heavy_columns, heavy_items, empty_columns;
     int64_t recomputed_columns;  /* learned sizing: columns that overflowed their predicted capacity */
+    int64_t nnzB_heavy;          /* nonzeros of B in the heavy (dense-slab) columns */
+    int64_t nnzC_heavy;          /* nonzeros of C in the heavy columns (-1 before symbolic) */
+    int64_t kernel_launches;     /* kernels this plan launched so far */
     double ms_plan, ms_symbolic, ms_numeric; /* device time of each phase (CUDA events) */
+    /* device time of kernel groups (CUDA events on the plan's stream):
+     * gather = A~ copy; sym/num light = all warp-hash bins; sym/num heavy = dense slabs */
+    double ms_gather, ms_sym_light, ms_sym_heavy, ms_num_light, ms_num_heavy;
 } spg_stats;
 
 typedef struct spg_plan spg_plan;

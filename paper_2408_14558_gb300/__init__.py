@@ -64,8 +64,10 @@ class spg_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "m", "k", "n", "nnzA", "nnzB", "P", "b", "products", "nnzC", "sum_H", "sum_dtilde",
         "fetch_blocks_total", "fetch_blocks_chosen", "gathered_nnz_exact", "gathered_nnz_block",
-        "light_columns", "heavy_columns", "heavy_items", "empty_columns", "recomputed_columns")] + [
-        ("ms_plan", ctypes.c_double), ("ms_symbolic", ctypes.c_double), ("ms_numeric", ctypes.c_double)]
+        "light_columns", "heavy_columns", "heavy_items", "empty_columns", "recomputed_columns",
+        "nnzB_heavy", "nnzC_heavy", "kernel_launches")] + [
+        (name, ctypes.c_double) for name in ("ms_plan", "ms_symbolic", "ms_numeric", "ms_gather", "ms_sym_light",
+                                             "ms_sym_heavy", "ms_num_light", "ms_num_heavy")]
 
 
 _lib = None

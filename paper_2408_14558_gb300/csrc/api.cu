@@ -71,6 +71,15 @@ extern "C" spg_status spgemm_plan_stats(const spg_plan *pc, spg_stats *st) {
             p->stats.ms_numeric = ms;
         cudaGetLastError();
     }
+    double *group_ms[5] = {&p->stats.ms_gather, &p->stats.ms_sym_light, &p->stats.ms_sym_heavy,
+                           &p->stats.ms_num_light, &p->stats.ms_num_heavy};
+    for (int g = 0; g < 5; g++) {
+        float ms = 0;
+        if (p->kev_used[g] && cudaEventElapsedTime(&ms, p->kev[2 * g], p->kev[2 * g + 1]) == cudaSuccess)
+            *group_ms[g] = ms;
+        cudaGetLastError();
+    }
+    p->stats.kernel_launches = p->launches;
     *st = p->stats;
     return read_dev_err(p, "stats");
 }

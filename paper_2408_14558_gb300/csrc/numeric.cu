@@ -257,7 +257,7 @@ static spg_status launch_num_light(spg_plan *p, const int32_t *list, int64_t cnt
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WARPS * 32, smem);
     if (occ < 1) occ = 1;
     int g = grid_for(cnt, WARPS, p->sm_count * occ);
-    kern<<<g, WARPS * 32, smem, p->st>>>(list, cnt, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq,
+    launch(p, kern, g, WARPS * 32, smem, list, cnt, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq,
                                          (const Acc *)p->Bv, p->At_colptr, p->At_row, (const Acc *)p->At_val,
                                          p->Ccolptr, (OutIdx *)C->rowidx, (Acc *)C->vals, p->d_err);
     return cuda_check(cudaGetLastError(), "numeric light");
@@ -266,6 +266,8 @@ static spg_status launch_num_light(spg_plan *p, const int32_t *list, int64_t cnt
 template <typename Acc, typename OutIdx>
 static spg_status numeric_typed(spg_plan *p, spg_csc *C) {
     spg_status s = SPG_OK;
+    const bool any_light = p->nbin_off[kMaxLightBin + 1] > p->nbin_off[1];
+    if (any_light) group_begin(p, kKNumLight);
     for (int bin = 1; bin <= kMaxLightBin && !s; bin++) {
         int64_t cnt = p->nbin_off[bin + 1] - p->nbin_off[bin];
         if (cnt == 0) continue;
@@ -279,6 +281,7 @@ static spg_status numeric_typed(spg_plan *p, spg_csc *C) {
             default: s = launch_num_light<11, 4, Acc, OutIdx>(p, list, cnt, C); break;
         }
     }
+    if (any_light) group_end(p, kKNumLight);
     if (s) return s;
     if (p->nitems > 0) {
         const int threads = 256;
@@ -291,10 +294,12 @@ static spg_status numeric_typed(spg_plan *p, spg_csc *C) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
         if (occ < 1) occ = 1;
         int g = grid_for(p->nitems, 1, p->sm_count * occ);
-        kern<<<g, threads, smem, p->st>>>(p->nitems, p->item_col, p->item_slab, p->item_cnt, p->item_off, p->hbits,
-                                          p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv,
-                                          p->At_colptr, p->At_row, (const Acc *)p->At_val, p->split, p->T, p->R,
-                                          p->Ccolptr, (OutIdx *)C->rowidx, (Acc *)C->vals, p->d_err);
+        group_begin(p, kKNumHeavy);
+        launch(p, kern, g, threads, smem, p->nitems, p->item_col, p->item_slab, p->item_cnt, p->item_off, p->hbits,
+               p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv, p->At_colptr, p->At_row,
+               (const Acc *)p->At_val, p->split, p->T, p->R, p->Ccolptr, (OutIdx *)C->rowidx, (Acc *)C->vals,
+               p->d_err);
+        group_end(p, kKNumHeavy);
         s = cuda_check(cudaGetLastError(), "numeric heavy");
     }
     return s;
@@ -308,7 +313,7 @@ spg_status run_numeric(spg_plan *p, spg_csc *C) {
         p->nbinlist = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(n + 1));
         if (!bn || !p->nbinlist) return SPG_OUT_OF_MEMORY;
         if (n > 0) {
-            k_rebin_numeric<<<grid_for(n, 256, p->sm_count * 8), 256, 0, st>>>(p->bin_of, p->nnzcol, n, bn);
+            launch(p, k_rebin_numeric, grid_for(n, 256, p->sm_count * 8), 256, 0, p->bin_of, p->nnzcol, n, bn);
             spg_status s = cuda_check(cudaGetLastError(), "rebin");
             if (s) return s;
             s = bin_columns(p, bn, p->nbinlist, p->nbin_off);

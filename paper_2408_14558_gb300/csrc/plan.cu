@@ -119,6 +119,7 @@ enum {
     kCntMaxAcol = 4,
     kCntBin0 = 8,  // kNumBins histogram counters
     kCntHeavyItems = 16,
+    kCntNnzBHeavy = 17,
     kCntSlots = 24
 };
 
@@ -432,7 +433,7 @@ spg_status bin_columns(spg_plan *p, const int8_t *bin_of, int32_t *list, int64_t
     spg_status s = cuda_check(cudaMemsetAsync(cnt, 0, sizeof(long long) * kNumBins, p->st), "bin memset");
     if (s) return s;
     int g = grid_for(n, 256, p->sm_count * 8);
-    k_bin_hist<<<g, 256, 0, p->st>>>(bin_of, n, cnt);
+    launch(p, k_bin_hist, g, 256, 0, bin_of, n, cnt);
     s = cuda_check(cudaMemcpyAsync(p->h_pinned, cnt, sizeof(long long) * kNumBins, cudaMemcpyDeviceToHost, p->st),
                    "bin readback");
     if (s) return s;
@@ -444,7 +445,7 @@ spg_status bin_columns(spg_plan *p, const int8_t *bin_of, int32_t *list, int64_t
     s = cuda_check(cudaMemcpyAsync(p->d_bincur, p->h_pinned, sizeof(long long) * kNumBins,
                                    cudaMemcpyHostToDevice, p->st), "bin cursor upload");
     if (s) return s;
-    k_bin_scatter<<<g, 256, 0, p->st>>>(bin_of, n, (long long *)p->d_bincur, list);
+    launch(p, k_bin_scatter, g, 256, 0, bin_of, n, (long long *)p->d_bincur, list);
     s = cuda_check(cudaGetLastError(), "bin scatter");
     if (s) return s;
     // the pinned buffer is reused by the next read-back: make sure the upload consumed it
@@ -453,11 +454,16 @@ spg_status bin_columns(spg_plan *p, const int8_t *bin_of, int32_t *list, int64_t
 
 // Heavy bins: slabs [t_lo, t_hi] of every heavy column from its row window.
 __global__ void k_heavy_nslab(const int32_t *list, int64_t nheavy, const int32_t *win_lo,
-                              const int32_t *win_hi, int R, int64_t *nslab) {
+                              const int32_t *win_hi, const int32_t *nnzb, int R, int64_t *nslab,
+                              long long *nnzb_heavy) {
+    long long sb = 0;
     for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += (int64_t)gridDim.x * blockDim.x) {
         int j = list[h];
         nslab[h] = (int64_t)(win_hi[j] / R - win_lo[j] / R + 1);
+        sb += nnzb[j];
     }
+    sb = warp_sum_ll(sb);
+    if ((threadIdx.x & 31) == 0 && sb) atomicAdd((unsigned long long *)nnzb_heavy, (unsigned long long)sb);
 }
 
 __global__ void k_heavy_items(const int32_t *list, int64_t nheavy, const int32_t *win_lo, int R,
@@ -544,9 +550,9 @@ static spg_status plan_build(spg_plan *p) {
     cudaEventRecord(p->ev[0], st);
 
     if (p->opt.validate) {
-        k_validate<<<grid_for(A.ncols * 32, 256, sm * 16), 256, 0, st>>>(A.colptr, p64A, A.rowidx, i64A, A.nrows,
+        launch(p, k_validate, grid_for(A.ncols * 32, 256, sm * 16), 256, 0, A.colptr, p64A, A.rowidx, i64A, A.nrows,
                                                                           A.ncols, A.nnz, p->d_err);
-        k_validate<<<grid_for(B.ncols * 32, 256, sm * 16), 256, 0, st>>>(B.colptr, p64B, B.rowidx, i64B, B.nrows,
+        launch(p, k_validate, grid_for(B.ncols * 32, 256, sm * 16), 256, 0, B.colptr, p64B, B.rowidx, i64B, B.nrows,
                                                                           B.ncols, B.nnz, p->d_err);
         LAUNCH_OK("validate");
         TRY(read_dev_err(p, "input validation"));
@@ -563,14 +569,14 @@ static spg_status plan_build(spg_plan *p) {
     p->fetch = (uint8_t *)ws_alloc(p, (size_t)(P * p->nfb + 1));
     if (!p->Dbits || !p->Hbits || !p->rankpre || !popc || !p->fetch) return SPG_OUT_OF_MEMORY;
     TRY(cuda_check(cudaMemsetAsync(p->Hbits, 0, sizeof(uint32_t) * (size_t)(P * W + 1), st), "memset H"));
-    if (W > 0) k_nonempty_bits<<<grid_for(W, 256, sm * 8), 256, 0, st>>>(A.colptr, p64A, k, W, p->Dbits);
-    if (n > 0) k_mark_H<<<grid_for(n * 32, 256, sm * 16), 256, 0, st>>>(B.colptr, p64B, B.rowidx, i64B, n, P, W, p->Hbits);
+    if (W > 0) launch(p, k_nonempty_bits, grid_for(W, 256, sm * 8), 256, 0, A.colptr, p64A, k, W, p->Dbits);
+    if (n > 0) launch(p, k_mark_H, grid_for(n * 32, 256, sm * 16), 256, 0, B.colptr, p64B, B.rowidx, i64B, n, P, W, p->Hbits);
     LAUNCH_OK("mark H");
 
     // --- step 2: D~_i = H_i & D, its ranks and Algorithm 2
     int64_t PW = (int64_t)P * W;
     if (PW > 0)
-        k_popc_HD<<<grid_for(PW, 256, sm * 8), 256, 0, st>>>(p->Hbits, p->Dbits, W, PW, popc,
+        launch(p, k_popc_HD, grid_for(PW, 256, sm * 8), 256, 0, p->Hbits, p->Dbits, W, PW, popc,
                                                             (long long *)(p->d_cnt + kCntSumH));
     TRY(scan_exclusive_i32(p, popc, p->rankpre, PW));
     // |D~| in total and per block: read the block boundaries of the scan
@@ -590,16 +596,16 @@ static spg_status plan_build(spg_plan *p) {
     p->At_colptr = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->ndt + 1));
     int64_t *glen = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->ndt + 1));
     if (!p->dtilde || !p->At_colptr || !glen) return SPG_OUT_OF_MEMORY;
-    if (PW > 0) k_dtilde<<<grid_for(PW, 256, sm * 8), 256, 0, st>>>(p->Hbits, p->Dbits, p->rankpre, W, PW, p->dtilde);
+    if (PW > 0) launch(p, k_dtilde, grid_for(PW, 256, sm * 8), 256, 0, p->Hbits, p->Dbits, p->rankpre, W, PW, p->dtilde);
     if (P * p->nfb > 0)
-        k_fetch<<<grid_for(P * p->nfb, 256, sm * 8), 256, 0, st>>>(
+        launch(p, k_fetch, grid_for(P * p->nfb, 256, sm * 8), 256, 0,
             p->Hbits, p->Dbits, p->rankpre, W, k, p->b, p->nfb, P, A.colptr, p64A, p->fetch,
             (long long *)(p->d_cnt + kCntFetchChosen), (long long *)(p->d_cnt + kCntVolBlock));
     LAUNCH_OK("dtilde / fetch");
 
     // --- step 3: gather A~
     if (p->ndt > 0)
-        k_gather_len<<<grid_for(p->ndt, 256, sm * 8), 256, 0, st>>>(p->dtilde, p->ndt, A.colptr, p64A, glen,
+        launch(p, k_gather_len, grid_for(p->ndt, 256, sm * 8), 256, 0, p->dtilde, p->ndt, A.colptr, p64A, glen,
                                                                   (long long *)(p->d_cnt + kCntMaxAcol));
     TRY(scan_exclusive_i64(p, glen, p->At_colptr, p->ndt));
     TRY(cuda_check(cudaMemcpyAsync(p->h_pinned, p->At_colptr + p->ndt, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "readback"));
@@ -617,23 +623,25 @@ static spg_status plan_build(spg_plan *p) {
     if (!p->At_row || !p->At_val || !p->Bq || !p->Bv) return SPG_OUT_OF_MEMORY;
     if (P * p->nfb > 0 && p->nAt > 0) {
         int g = grid_for(P * p->nfb, 1, sm * 8);
+        group_begin(p, kKGather);
         if (p->acc_f64)
-            k_gather_copy<double><<<g, 256, 0, st>>>(p->Hbits, p->Dbits, p->rankpre, W, k, p->b, p->nfb, P, p->fetch,
-                                                     p->dtilde, A.colptr, p64A, A.rowidx, i64A, A.vals, A.val_type,
-                                                     p->At_colptr, p->At_row, (double *)p->At_val);
+            launch(p, k_gather_copy<double>, g, 256, 0, p->Hbits, p->Dbits, p->rankpre, W, k, p->b, p->nfb, P,
+                   p->fetch, p->dtilde, A.colptr, p64A, A.rowidx, i64A, A.vals, A.val_type, p->At_colptr,
+                   p->At_row, (double *)p->At_val);
         else
-            k_gather_copy<long long><<<g, 256, 0, st>>>(p->Hbits, p->Dbits, p->rankpre, W, k, p->b, p->nfb, P,
-                                                        p->fetch, p->dtilde, A.colptr, p64A, A.rowidx, i64A, A.vals,
-                                                        A.val_type, p->At_colptr, p->At_row, (long long *)p->At_val);
+            launch(p, k_gather_copy<long long>, g, 256, 0, p->Hbits, p->Dbits, p->rankpre, W, k, p->b, p->nfb, P,
+                   p->fetch, p->dtilde, A.colptr, p64A, A.rowidx, i64A, A.vals, A.val_type, p->At_colptr,
+                   p->At_row, (long long *)p->At_val);
+        group_end(p, kKGather);
         LAUNCH_OK("gather");
     }
     if (n > 0) {
         int g = grid_for(n * 32, 256, sm * 16);
         if (p->acc_f64)
-            k_remap_B<double><<<g, 256, 0, st>>>(B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P, p->Hbits,
+            launch(p, k_remap_B<double>, g, 256, 0, B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P, p->Hbits,
                                                  p->Dbits, p->rankpre, W, p->Bq, (double *)p->Bv);
         else
-            k_remap_B<long long><<<g, 256, 0, st>>>(B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P,
+            launch(p, k_remap_B<long long>, g, 256, 0, B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P,
                                                     p->Hbits, p->Dbits, p->rankpre, W, p->Bq, (long long *)p->Bv);
         LAUNCH_OK("remap B");
     }
@@ -652,7 +660,7 @@ static spg_status plan_build(spg_plan *p) {
         !p->nnzcol || !p->Ccolptr)
         return SPG_OUT_OF_MEMORY;
     if (n > 0) {
-        k_col_stats<<<grid_for(n * 32, 256, sm * 16), 256, 0, st>>>(
+        launch(p, k_col_stats, grid_for(n * 32, 256, sm * 16), 256, 0,
             B.colptr, p64B, n, p->Bq, p->At_colptr, p->At_row, p->light_max, p->flops, p->win_lo, p->win_hi,
             p->nnzb, p->maxa, p->bin_of, (long long *)(p->d_cnt + kCntBin0), (long long *)(p->d_cnt + kCntProducts));
         LAUNCH_OK("column stats");
@@ -668,7 +676,8 @@ static spg_status plan_build(spg_plan *p) {
         int64_t *nslab = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
         p->item_first = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
         if (!nslab || !p->item_first) return SPG_OUT_OF_MEMORY;
-        k_heavy_nslab<<<grid_for(p->nheavy, 256, sm * 8), 256, 0, st>>>(hl, p->nheavy, p->win_lo, p->win_hi, p->R, nslab);
+        launch(p, k_heavy_nslab, grid_for(p->nheavy, 256, sm * 8), 256, 0, hl, p->nheavy, p->win_lo, p->win_hi,
+               p->nnzb, p->R, nslab, (long long *)(p->d_cnt + kCntNnzBHeavy));
         TRY(scan_exclusive_i64(p, nslab, p->item_first, p->nheavy));
         TRY(cuda_check(cudaMemcpyAsync(p->h_pinned, p->item_first + p->nheavy, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "items"));
         TRY(cuda_check(cudaStreamSynchronize(st), "items"));
@@ -681,10 +690,10 @@ static spg_status plan_build(spg_plan *p) {
         p->split = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->ndt + 1) * (size_t)(p->T + 1));
         if (!p->item_col || !p->item_slab || !p->item_cnt || !p->item_off || !p->hbits || !p->split)
             return SPG_OUT_OF_MEMORY;
-        k_heavy_items<<<grid_for(p->nheavy, 256, sm * 8), 256, 0, st>>>(hl, p->nheavy, p->win_lo, p->R, p->item_first,
+        launch(p, k_heavy_items, grid_for(p->nheavy, 256, sm * 8), 256, 0, hl, p->nheavy, p->win_lo, p->R, p->item_first,
                                                                         p->item_col, p->item_slab);
         if (p->ndt > 0)
-            k_split<<<grid_for(p->ndt * (p->T + 1), 256, sm * 16), 256, 0, st>>>(p->At_colptr, p->At_row, p->ndt, p->T,
+            launch(p, k_split, grid_for(p->ndt * (p->T + 1), 256, sm * 16), 256, 0, p->At_colptr, p->At_row, p->ndt, p->T,
                                                                                  p->R, p->split);
         LAUNCH_OK("heavy items");
     }
@@ -707,9 +716,12 @@ static spg_status plan_build(spg_plan *p) {
     S.heavy_columns = p->nheavy;
     S.light_columns = n - S.empty_columns - S.heavy_columns;
     S.heavy_items = p->nitems;
+    S.nnzB_heavy = p->h_pinned[kCntNnzBHeavy];
+    S.nnzC_heavy = -1;
     float ms = 0;
     cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]);
     S.ms_plan = ms;
+    if (p->kev_used[kKGather] && cudaEventElapsedTime(&ms, p->kev[0], p->kev[1]) == cudaSuccess) S.ms_gather = ms;
     return read_dev_err(p, "plan");
 }
 
@@ -798,6 +810,7 @@ extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_
     if (!s) s = cuda_check(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev), "attr");
     if (!s) s = cuda_check(cudaMallocHost(&p->h_pinned, sizeof(int64_t) * 64), "cudaMallocHost");
     for (int i = 0; i < 8 && !s; i++) s = cuda_check(cudaEventCreate(&p->ev[i]), "event");
+    for (int i = 0; i < 10 && !s; i++) s = cuda_check(cudaEventCreate(&p->kev[i]), "event");
     if (!s) s = plan_build(p);
     if (s) {
         std::string keep = last_error_str();
@@ -815,6 +828,8 @@ extern "C" spg_status spgemm_plan_destroy(spg_plan *p) {
     cudaStreamSynchronize(p->st);
     for (int i = 0; i < 8; i++)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    for (int i = 0; i < 10; i++)
+        if (p->kev[i]) cudaEventDestroy(p->kev[i]);
     if (p->h_pinned) cudaFreeHost(p->h_pinned);
     delete p;
     return SPG_OK;

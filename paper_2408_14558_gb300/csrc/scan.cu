@@ -120,9 +120,9 @@ static spg_status scan_impl(spg_plan *p, const T *in, int64_t *out, int64_t n) {
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     long long *part = (long long *)ws_alloc(p, sizeof(long long) * (size_t)(ntiles + 1));
     if (!part) return SPG_OUT_OF_MEMORY;
-    k_scan_reduce<T><<<(unsigned)ntiles, kScanThreads, 0, p->st>>>(in, n, part);
-    k_scan_partials<<<1, 1024, 0, p->st>>>(part, ntiles, part + ntiles);
-    k_scan_tiles<T><<<(unsigned)ntiles, kScanThreads, 0, p->st>>>(in, n, part, part + ntiles, out);
+    launch(p, k_scan_reduce<T>, (unsigned)ntiles, kScanThreads, 0, in, n, part);
+    launch(p, k_scan_partials, 1, 1024, 0, part, ntiles, part + ntiles);
+    launch(p, k_scan_tiles<T>, (unsigned)ntiles, kScanThreads, 0, in, n, part, part + ntiles, out);
     return cuda_check(cudaGetLastError(), "scan launch");
 }
 

@@ -108,10 +108,35 @@ struct spg_plan {
     int64_t nbin_off[spg::kNumBins + 1] = {0};
 
     spg_stats stats{};
+    // ev[0..1] plan, ev[2..3] symbolic, ev[4..5] numeric; kev[2g], kev[2g+1]
+    // bracket kernel group g (see KernelGroup)
     cudaEvent_t ev[8] = {nullptr};
+    cudaEvent_t kev[10] = {nullptr};
+    bool kev_used[5] = {false, false, false, false, false};
+    int64_t launches = 0;
 };
 
 namespace spg {
+
+// Every kernel of the library is launched through here, on the plan's
+// stream, so that the plan can report how many kernels it ran.
+template <typename... KArgs, typename... Args>
+inline void launch(spg_plan *p, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args &&...args) {
+    p->launches++;
+    kern<<<grid, block, smem, p->st>>>(static_cast<KArgs>(args)...);
+}
+
+// Slot of plan->d_cnt that collects nnz(C) of the heavy columns (the other
+// slots are used by the planning kernels).
+constexpr int kCntNnzCHeavySlot = 18;
+
+// Kernel groups timed with their own event pair.
+enum KernelGroup { kKGather = 0, kKSymLight = 1, kKSymHeavy = 2, kKNumLight = 3, kKNumHeavy = 4 };
+inline void group_begin(spg_plan *p, int g) {
+    cudaEventRecord(p->kev[2 * g], p->st);
+    p->kev_used[g] = true;
+}
+inline void group_end(spg_plan *p, int g) { cudaEventRecord(p->kev[2 * g + 1], p->st); }
 
 // ---- host helpers (plan.cu)
 void set_error(const char *fmt, ...);

@@ -102,7 +102,9 @@ __global__ void __launch_bounds__(256)
 
 // Per heavy column: place each slab after the ones above it, total = nnz_j.
 __global__ void k_heavy_offsets(const int32_t *list, int64_t nheavy, const int64_t *item_first,
-                                const int32_t *item_cnt, int64_t *item_off, int64_t *nnzcol) {
+                                const int32_t *item_cnt, int64_t *item_off, int64_t *nnzcol,
+                                long long *nnzc_heavy) {
+    long long sum = 0;
     for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += (int64_t)gridDim.x * blockDim.x) {
         int64_t off = 0;
         for (int64_t it = item_first[h]; it < item_first[h + 1]; it++) {
@@ -110,7 +112,10 @@ __global__ void k_heavy_offsets(const int32_t *list, int64_t nheavy, const int64
             off += item_cnt[it];
         }
         nnzcol[list[h]] = off;
+        sum += off;
     }
+    sum = warp_sum_ll(sum);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd((unsigned long long *)nnzc_heavy, (unsigned long long)sum);
 }
 
 template <int LOGS, int WARPS>
@@ -122,8 +127,8 @@ static spg_status launch_sym_light(spg_plan *p, const int32_t *list, int64_t cnt
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WARPS * 32, smem);
     if (occ < 1) occ = 1;
     int g = grid_for(cnt, WARPS, p->sm_count * occ);
-    kern<<<g, WARPS * 32, smem, p->st>>>(list, cnt, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr,
-                                         p->At_row, p->nnzcol, p->d_err);
+    launch(p, kern, g, WARPS * 32, smem, list, cnt, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr,
+           p->At_row, p->nnzcol, p->d_err);
     return cuda_check(cudaGetLastError(), "symbolic light");
 }
 
@@ -132,7 +137,10 @@ spg_status run_symbolic(spg_plan *p) {
     const int64_t n = p->n;
     spg_status s = cuda_check(cudaMemsetAsync(p->nnzcol, 0, sizeof(int64_t) * (size_t)(n + 1), st), "memset");
     if (s) return s;
+    s = cuda_check(cudaMemsetAsync(p->d_cnt + kCntNnzCHeavySlot, 0, sizeof(int64_t), st), "memset");
+    if (s) return s;
     cudaEventRecord(p->ev[2], st);
+    if (p->bin_off[kMaxLightBin + 1] > p->bin_off[1]) group_begin(p, kKSymLight);
     for (int bin = 1; bin <= kMaxLightBin && !s; bin++) {
         int64_t cnt = p->bin_off[bin + 1] - p->bin_off[bin];
         if (cnt == 0) continue;
@@ -146,6 +154,7 @@ spg_status run_symbolic(spg_plan *p) {
             default: s = launch_sym_light<11, 8>(p, list, cnt); break;
         }
     }
+    if (p->bin_off[kMaxLightBin + 1] > p->bin_off[1]) group_end(p, kKSymLight);
     if (s) return s;
     if (p->nitems > 0) {
         const int threads = 256;
@@ -155,11 +164,14 @@ spg_status run_symbolic(spg_plan *p) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sym_heavy, threads, smem);
         if (occ < 1) occ = 1;
         int g = grid_for(p->nitems, 1, p->sm_count * occ);
-        k_sym_heavy<<<g, threads, smem, st>>>(p->nitems, p->item_col, p->item_slab, p->B.colptr,
-                                              p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr, p->At_row, p->split,
-                                              p->T, p->R, p->hbits, p->item_cnt);
-        k_heavy_offsets<<<grid_for(p->nheavy, 256, p->sm_count * 8), 256, 0, st>>>(
-            p->binlist + p->bin_off[kBinHeavy], p->nheavy, p->item_first, p->item_cnt, p->item_off, p->nnzcol);
+        group_begin(p, kKSymHeavy);
+        launch(p, k_sym_heavy, g, threads, smem, p->nitems, p->item_col, p->item_slab, p->B.colptr,
+               p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr, p->At_row, p->split, p->T, p->R, p->hbits,
+               p->item_cnt);
+        group_end(p, kKSymHeavy);
+        launch(p, k_heavy_offsets, grid_for(p->nheavy, 256, p->sm_count * 8), 256, 0,
+               p->binlist + p->bin_off[kBinHeavy], p->nheavy, p->item_first, p->item_cnt, p->item_off, p->nnzcol,
+               (long long *)(p->d_cnt + kCntNnzCHeavySlot));
         s = cuda_check(cudaGetLastError(), "symbolic heavy");
         if (s) return s;
     }
@@ -168,10 +180,14 @@ spg_status run_symbolic(spg_plan *p) {
     cudaEventRecord(p->ev[3], st);
     s = cuda_check(cudaMemcpyAsync(p->h_pinned, p->Ccolptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "nnz readback");
     if (s) return s;
+    s = cuda_check(cudaMemcpyAsync(p->h_pinned + 1, p->d_cnt + kCntNnzCHeavySlot, sizeof(int64_t),
+                                   cudaMemcpyDeviceToHost, st), "nnz readback");
+    if (s) return s;
     s = read_dev_err(p, "symbolic");
     if (s) return s;
     p->nnzC = p->h_pinned[0];
     p->stats.nnzC = p->nnzC;
+    p->stats.nnzC_heavy = p->h_pinned[1];
     float ms = 0;
     cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]);
     p->stats.ms_symbolic = ms;
