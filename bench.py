@@ -326,6 +326,9 @@ def main(argv=None):
             "path_roofline": {"compulsory_bytes_per_step": comp, "achieved": path_gbs, "frac": path_gbs / peak,
                               "unit": "GB/s"},
             "kernel_ms_per_step": {k: round(v, 4) for k, v in per_group.items()},
+            "kernel_ms_per_run": {label: {gname: round(statistics.mean(sts[ri]["ms_" + gname] for sts in stats), 4)
+                                          for gname in groups + ["plan", "symbolic", "numeric"]}
+                                  for ri, label in enumerate(("f64", "int64"))},
             "phase_ms_per_step": {ph: statistics.mean(sum(st["ms_" + ph] for st in sts) for sts in stats)
                                   for ph in ("plan", "symbolic", "numeric")},
             "gpu_launches": launches, "clocks": clk}

@@ -90,7 +90,7 @@ typedef struct {
     int64_t b;              /* fetch-block width in column ids of A, >= 1 */
     int32_t validate;       /* 1: check that A and B are canonical */
     int32_t light_max;      /* largest per-column bound handled by the warp hash bins (power of two, 32..1024; 0 = 1024) */
-    int32_t slab_rows;      /* rows per dense slab of the heavy bins (power of two, 1024..16384; 0 = 8192) */
+    int32_t slab_rows;      /* rows per base slab of the heavy bins (power of two, 1024..16384; 0 = 4096) */
     int32_t reserved;
     void *stream;           /* cudaStream_t */
     spg_alloc_fn alloc;

@@ -8,6 +8,7 @@
 //               slab gives every present row its rank, products accumulate at
 //               acc[rank] in shared memory, and the slab is written out in row
 //               order with no sort
+#include "cta_products.cuh"
 #include "spg_internal.cuh"
 
 namespace spg {
@@ -46,6 +47,45 @@ __device__ __forceinline__ int cta_scan_popc(const uint32_t *bits, int *pre, int
     for (int w = w0; w < min(RW, w0 + per); w++) {
         pre[w] = run;
         run += __popc(bits[w]);
+    }
+    int total = wsum[32];
+    __syncthreads();
+    return total;
+}
+
+// The same scan over packed (word, prefix) pairs: fills bp[w].y.
+__device__ __forceinline__ int cta_scan_popc_packed(uint2 *bp, int n, int *wsum) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int per = (n + nt - 1) / nt;
+    const int w0 = tid * per;
+    int local = 0;
+    for (int w = w0; w < min(n, w0 + per); w++) local += __popc(bp[w].x);
+    const int lane = tid & 31, wid = tid >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = nt >> 5;
+        int v = lane < nw ? wsum[lane] : 0;
+        int vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(kFull, vi, o);
+            if (lane >= o) vi += t;
+        }
+        if (lane < nw) wsum[lane] = vi - v;
+        if (lane == 31) wsum[32] = vi;
+    }
+    __syncthreads();
+    int run = wsum[wid] + incl - local;
+    for (int w = w0; w < min(n, w0 + per); w++) {
+        bp[w].y = (uint32_t)run;
+        run += __popc(bp[w].x);
     }
     int total = wsum[32];
     __syncthreads();
@@ -151,34 +191,41 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
+// One CTA per numeric item: records [r0, r0 + nr) of one heavy column (base
+// slabs t0 .. t0 + nr - 1) holding cnt <= cap entries of C.  The symbolic
+// bitmaps of the records give every present row its rank (pre[word] + popc of
+// the lower bits); products accumulate at acc[rank]; the item is then written
+// at its final place in C, values as one coalesced run and rows word by word.
 template <typename Acc, typename OutIdx>
 __global__ void __launch_bounds__(256)
-    k_num_heavy(int64_t nitems, const int32_t *__restrict__ item_col, const int32_t *__restrict__ item_slab,
-                const int32_t *__restrict__ item_cnt, const int64_t *__restrict__ item_off,
+    k_num_heavy(int64_t nitems, const int32_t *__restrict__ num_rec0, const int32_t *__restrict__ num_nrec,
+                const int32_t *__restrict__ rec_col, const int32_t *__restrict__ rec_slab,
+                const int32_t *__restrict__ rec_cnt, const int64_t *__restrict__ rec_off,
                 const uint32_t *__restrict__ hbits, const void *Bcolptr, int p64, const int32_t *__restrict__ Bq,
                 const Acc *__restrict__ Bv, const int64_t *__restrict__ At_colptr,
                 const int32_t *__restrict__ At_row, const Acc *__restrict__ At_val,
-                const int32_t *__restrict__ split, int T, int R, const int64_t *__restrict__ Ccolptr,
+                const int32_t *__restrict__ split, int T, int R, int cap, const int64_t *__restrict__ Ccolptr,
                 OutIdx *__restrict__ Crow, Acc *__restrict__ Cval, int *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RW = R >> 5;
-    const int nw = blockDim.x >> 5;
-    WarpSeg<Acc> *segs = (WarpSeg<Acc> *)smem_raw;
-    Acc *acc = (Acc *)(segs + nw);
-    uint32_t *bits = (uint32_t *)(acc + R);
-    int *pre = (int *)(bits + RW);
+    CtaBatch<Acc> &sb = *(CtaBatch<Acc> *)smem_raw;
+    Acc *acc = (Acc *)(smem_raw + ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15));
+    uint2 *bp = (uint2 *)(acc + cap);  // (bitmap word, exclusive prefix of popcounts)
     __shared__ int wsum[33];
     __shared__ int bad_sh;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) bad_sh = 0;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int j = item_col[it], t = item_slab[it];
-        const uint32_t *src = hbits + it * RW;
-        for (int w = threadIdx.x; w < RW; w += blockDim.x) bits[w] = src[w];
+        const int r0 = num_rec0[it], nr = num_nrec[it];
+        const int j = rec_col[r0], t0 = rec_slab[r0];
+        const int nwords = nr * RW;
+        const uint32_t *src = hbits + (int64_t)r0 * RW;
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) bp[w].x = src[w];
         __syncthreads();
-        const int cnt = cta_scan_popc(bits, pre, RW, wsum);
-        if (cnt != item_cnt[it]) {
-            // the slab's room in C was sized from item_cnt: never write past it
+        const int cnt = cta_scan_popc_packed(bp, nwords, wsum);
+        int want = 0;
+        for (int rr = 0; rr < nr; rr++) want += rec_cnt[r0 + rr];
+        if (cnt != want || cnt > cap) {
+            // the item's room in C was sized from rec_cnt: never write past it
             if (threadIdx.x == 0) bad_sh = 1;
             __syncthreads();
             continue;
@@ -186,40 +233,38 @@ __global__ void __launch_bounds__(256)
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) acc[i] = Acc(0);
         __syncthreads();
         const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
-        const int wbase = t * RW;
+        const int wbase = t0 * RW;
         bool miss = false;
-        for (int64_t c0 = p0 + (int64_t)wid * 32; c0 < p1; c0 += (int64_t)nw * 32) {
-            warp_products<true, Acc>(
-                c0, min(c0 + 32, p1), lane, segs[wid], At_row, At_val,
-                [&](int64_t p, long long &st, int &len, Acc &bv) {
-                    int q = Bq[p];
-                    if (q >= 0) {
-                        const int32_t *sp = split + (int64_t)q * (T + 1) + t;
-                        int a = sp[0], b = sp[1];
-                        st = At_colptr[q] + a;
-                        len = b - a;
-                        bv = Bv[p];
-                    }
-                },
-                [&](int r, Acc v) {
-                    int w = (r >> 5) - wbase;
-                    uint32_t word = bits[w];
-                    uint32_t below = word & ((1u << (r & 31)) - 1u);
-                    if (!((word >> (r & 31)) & 1u)) miss = true;
-                    else atomic_add_acc(acc + pre[w] + __popc(below), v);
-                });
-        }
+        cta_products<true, 2, Acc>(
+            p0, p1, sb, At_row, At_val,
+            [&](int64_t p, long long &st, int &len, Acc &bv) {
+                int q = Bq[p];
+                if (q >= 0) {
+                    const int32_t *sp = split + (int64_t)q * (T + 1);
+                    int a = sp[t0], b = sp[t0 + nr];
+                    st = At_colptr[q] + a;
+                    len = b - a;
+                    bv = Bv[p];
+                }
+            },
+            [&](int r, Acc v) {
+                const uint2 x = bp[(r >> 5) - wbase];
+                if (!((x.x >> (r & 31)) & 1u))
+                    miss = true;
+                else
+                    atomic_add_acc(acc + x.y + __popc(x.x & ((1u << (r & 31)) - 1u)), v);
+            });
         if (miss) bad_sh = 1;
-        __syncthreads();
-        const int64_t base = Ccolptr[j] + item_off[it];
+        // cta_products ends with a barrier: acc is complete
+        const int64_t base = Ccolptr[j] + rec_off[r0];
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) Cval[base + i] = acc[i];
-        const OutIdx rbase = (OutIdx)t * R;
-        for (int w = threadIdx.x; w < RW; w += blockDim.x) {
-            uint32_t word = bits[w];
-            int64_t pos = base + pre[w];
+        const int64_t rbase = (int64_t)t0 * R;
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+            uint32_t word = bp[w].x;
+            int64_t pos = base + bp[w].y;
             while (word) {
                 int bb = __ffs(word) - 1;
-                Crow[pos++] = rbase + (OutIdx)(w * 32 + bb);
+                Crow[pos++] = (OutIdx)(rbase + w * 32 + bb);
                 word &= word - 1u;
             }
         }
@@ -283,22 +328,21 @@ static spg_status numeric_typed(spg_plan *p, spg_csc *C) {
     }
     if (any_light) group_end(p, kKNumLight);
     if (s) return s;
-    if (p->nitems > 0) {
+    if (p->nnum > 0) {
         const int threads = 256;
-        const int RW = p->R / 32;
-        size_t smem = sizeof(WarpSeg<Acc>) * (threads / 32) + sizeof(Acc) * (size_t)p->R +
-                      sizeof(uint32_t) * (size_t)RW + sizeof(int) * (size_t)(RW + 2);
+        size_t smem = ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15) + sizeof(Acc) * (size_t)p->num_cap +
+                      sizeof(uint2) * (size_t)kNumMaxWords;
         auto kern = k_num_heavy<Acc, OutIdx>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int occ = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
         if (occ < 1) occ = 1;
-        int g = grid_for(p->nitems, 1, p->sm_count * occ);
+        int g = grid_for(p->nnum, 1, p->sm_count * occ);
         group_begin(p, kKNumHeavy);
-        launch(p, kern, g, threads, smem, p->nitems, p->item_col, p->item_slab, p->item_cnt, p->item_off, p->hbits,
-               p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv, p->At_colptr, p->At_row,
-               (const Acc *)p->At_val, p->split, p->T, p->R, p->Ccolptr, (OutIdx *)C->rowidx, (Acc *)C->vals,
-               p->d_err);
+        launch(p, kern, g, threads, smem, p->nnum, p->num_rec0, p->num_nrec, p->rec_col, p->rec_slab, p->rec_cnt,
+               p->rec_off, p->hbits, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv,
+               p->At_colptr, p->At_row, (const Acc *)p->At_val, p->split, p->T, p->R, p->num_cap, p->Ccolptr,
+               (OutIdx *)C->rowidx, (Acc *)C->vals, p->d_err);
         group_end(p, kKNumHeavy);
         s = cuda_check(cudaGetLastError(), "numeric heavy");
     }

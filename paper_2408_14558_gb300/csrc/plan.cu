@@ -392,64 +392,88 @@ __global__ void k_col_stats(const void *Bcolptr, int p64, int64_t n, const int32
     if (threadIdx.x == 0 && prod_sh) atomicAdd((unsigned long long *)products, (unsigned long long)prod_sh);
 }
 
-__global__ void k_bin_hist(const int8_t *bin_of, int64_t n, long long *bincnt) {
-    __shared__ int hist[kNumBins];
-    if (threadIdx.x < kNumBins) hist[threadIdx.x] = 0;
-    __syncthreads();
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&hist[bin_of[j]], 1);
-    __syncthreads();
-    if (threadIdx.x < kNumBins && hist[threadIdx.x])
-        atomicAdd((unsigned long long *)&bincnt[threadIdx.x], (unsigned long long)hist[threadIdx.x]);
-}
+// Stable counting sort of column ids by bin.  Columns are cut into chunks of
+// kBinChunk; cnt[bin * nchunks + chunk] counts each chunk's columns per bin, a
+// scan of cnt (bin-major) gives every (bin, chunk) its first slot, and the
+// scatter keeps column order inside each chunk.  Within a bin the columns are
+// therefore ascending, so the heavy items of block i run before those of
+// block i + 1 and share A~_i in L2.
+constexpr int kBinChunk = 2048;
 
-// Counting sort of column ids by bin: a CTA reserves one range per bin with a
-// single global atomic, then places its columns inside it.
-__global__ void k_bin_scatter(const int8_t *bin_of, int64_t n, long long *cursor, int32_t *list) {
-    __shared__ int cnt[kNumBins];
-    __shared__ long long base[kNumBins];
-    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < n; j0 += (int64_t)gridDim.x * blockDim.x) {
-        if (threadIdx.x < kNumBins) cnt[threadIdx.x] = 0;
+__global__ void k_bin_chunk_count(const int8_t *bin_of, int64_t n, int64_t nchunks, int32_t *cnt) {
+    __shared__ int h[kNumBins];
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        if (threadIdx.x < kNumBins) h[threadIdx.x] = 0;
         __syncthreads();
-        int64_t j = j0 + threadIdx.x;
-        int bin = -1, local = 0;
-        if (j < n) {
-            bin = bin_of[j];
-            local = atomicAdd(&cnt[bin], 1);
+        const int64_t j0 = c * kBinChunk;
+        for (int i = threadIdx.x; i < kBinChunk; i += blockDim.x) {
+            int64_t j = j0 + i;
+            if (j < n) atomicAdd(&h[bin_of[j]], 1);
         }
         __syncthreads();
-        if (threadIdx.x < kNumBins && cnt[threadIdx.x])
-            base[threadIdx.x] = (long long)atomicAdd((unsigned long long *)&cursor[threadIdx.x],
-                                                     (unsigned long long)cnt[threadIdx.x]);
-        __syncthreads();
-        if (bin >= 0) list[base[bin] + local] = (int32_t)j;
+        if (threadIdx.x < kNumBins) cnt[(int64_t)threadIdx.x * nchunks + c] = h[threadIdx.x];
         __syncthreads();
     }
 }
 
+__global__ void __launch_bounds__(256)
+    k_bin_chunk_scatter(const int8_t *bin_of, int64_t n, int64_t nchunks, const int64_t *off, int32_t *list) {
+    __shared__ int run[kNumBins];
+    __shared__ int wcnt[8][kNumBins];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        if (threadIdx.x < kNumBins) run[threadIdx.x] = 0;
+        __syncthreads();
+        for (int r = 0; r < kBinChunk; r += blockDim.x) {
+            const int64_t j = c * kBinChunk + r + threadIdx.x;
+            const int b = j < n ? bin_of[j] : -1;
+            int myrank = 0;
+#pragma unroll
+            for (int bb = 0; bb < kNumBins; bb++) {
+                unsigned m = __ballot_sync(kFull, b == bb);
+                if (b == bb) myrank = __popc(m & ((1u << lane) - 1u));
+                if (lane == 0) wcnt[wid][bb] = __popc(m);
+            }
+            __syncthreads();
+            if (b >= 0) {
+                int before = run[b];
+                for (int w = 0; w < wid; w++) before += wcnt[w][b];
+                list[off[(int64_t)b * nchunks + c] + before + myrank] = (int32_t)j;
+            }
+            __syncthreads();
+            if (threadIdx.x < kNumBins) {
+                int tot = 0;
+                for (int w = 0; w < nw; w++) tot += wcnt[w][threadIdx.x];
+                run[threadIdx.x] += tot;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 spg_status bin_columns(spg_plan *p, const int8_t *bin_of, int32_t *list, int64_t *off_host) {
-    int64_t n = p->n;
-    long long *cnt = (long long *)(p->d_cnt + kCntBin0);
-    spg_status s = cuda_check(cudaMemsetAsync(cnt, 0, sizeof(long long) * kNumBins, p->st), "bin memset");
+    const int64_t n = p->n;
+    const int64_t nchunks = (n + kBinChunk - 1) / kBinChunk;
+    const int64_t ncnt = nchunks * kNumBins;
+    int32_t *cnt = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(ncnt + 1));
+    int64_t *off = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(ncnt + 1));
+    if (!cnt || !off) return SPG_OUT_OF_MEMORY;
+    const int g = grid_for(nchunks, 1, p->sm_count * 8);
+    launch(p, k_bin_chunk_count, g, 256, 0, bin_of, n, nchunks, cnt);
+    spg_status s = scan_exclusive_i32(p, cnt, off, ncnt);
     if (s) return s;
-    int g = grid_for(n, 256, p->sm_count * 8);
-    launch(p, k_bin_hist, g, 256, 0, bin_of, n, cnt);
-    s = cuda_check(cudaMemcpyAsync(p->h_pinned, cnt, sizeof(long long) * kNumBins, cudaMemcpyDeviceToHost, p->st),
-                   "bin readback");
+    for (int b = 0; b <= kNumBins; b++) {
+        s = cuda_check(cudaMemcpyAsync(p->h_pinned + b, off + (int64_t)b * nchunks, sizeof(int64_t),
+                                       cudaMemcpyDeviceToHost, p->st), "bin readback");
+        if (s) return s;
+    }
+    launch(p, k_bin_chunk_scatter, g, 256, 0, bin_of, n, nchunks, (const int64_t *)off, list);
+    s = cuda_check(cudaGetLastError(), "bin scatter");
     if (s) return s;
     s = cuda_check(cudaStreamSynchronize(p->st), "bin readback");
     if (s) return s;
-    off_host[0] = 0;
-    for (int b = 0; b < kNumBins; b++) off_host[b + 1] = off_host[b] + p->h_pinned[b];
-    for (int b = 0; b < kNumBins; b++) p->h_pinned[b] = off_host[b];
-    s = cuda_check(cudaMemcpyAsync(p->d_bincur, p->h_pinned, sizeof(long long) * kNumBins,
-                                   cudaMemcpyHostToDevice, p->st), "bin cursor upload");
-    if (s) return s;
-    launch(p, k_bin_scatter, g, 256, 0, bin_of, n, (long long *)p->d_bincur, list);
-    s = cuda_check(cudaGetLastError(), "bin scatter");
-    if (s) return s;
-    // the pinned buffer is reused by the next read-back: make sure the upload consumed it
-    return cuda_check(cudaStreamSynchronize(p->st), "bin scatter");
+    for (int b = 0; b <= kNumBins; b++) off_host[b] = p->h_pinned[b];
+    return SPG_OK;
 }
 
 // Heavy bins: slabs [t_lo, t_hi] of every heavy column from its row window.
@@ -466,14 +490,29 @@ __global__ void k_heavy_nslab(const int32_t *list, int64_t nheavy, const int32_t
     if ((threadIdx.x & 31) == 0 && sb) atomicAdd((unsigned long long *)nnzb_heavy, (unsigned long long)sb);
 }
 
-__global__ void k_heavy_items(const int32_t *list, int64_t nheavy, const int32_t *win_lo, int R,
-                              const int64_t *item_first, int32_t *item_col, int32_t *item_slab) {
+// Records (column, base slab) of every heavy column, and the number of
+// symbolic items (groups of <= smr consecutive records) it needs.
+__global__ void k_heavy_records(const int32_t *list, int64_t nheavy, const int32_t *win_lo, int R, int smr,
+                                const int64_t *rec_first, int32_t *rec_col, int32_t *rec_slab, int64_t *nsym) {
     for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += (int64_t)gridDim.x * blockDim.x) {
         int j = list[h];
         int t0 = win_lo[j] / R;
-        for (int64_t it = item_first[h]; it < item_first[h + 1]; it++) {
-            item_col[it] = j;
-            item_slab[it] = t0 + (int)(it - item_first[h]);
+        for (int64_t r = rec_first[h]; r < rec_first[h + 1]; r++) {
+            rec_col[r] = j;
+            rec_slab[r] = t0 + (int)(r - rec_first[h]);
+        }
+        nsym[h] = (rec_first[h + 1] - rec_first[h] + smr - 1) / smr;
+    }
+}
+
+__global__ void k_sym_items(int64_t nheavy, int smr, const int64_t *rec_first, const int64_t *sym_first,
+                            int32_t *sym_rec0, int32_t *sym_nrec) {
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = rec_first[h], e = rec_first[h + 1];
+        for (int64_t it = sym_first[h]; it < sym_first[h + 1]; it++) {
+            sym_rec0[it] = (int32_t)r;
+            sym_nrec[it] = (int32_t)min((int64_t)smr, e - r);
+            r += smr;
         }
     }
 }
@@ -674,24 +713,39 @@ static spg_status plan_build(spg_plan *p) {
     if (p->nheavy > 0) {
         const int32_t *hl = p->binlist + p->bin_off[kBinHeavy];
         int64_t *nslab = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
-        p->item_first = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
-        if (!nslab || !p->item_first) return SPG_OUT_OF_MEMORY;
+        int64_t *nsym = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
+        int64_t *sym_first = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
+        p->rec_first = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
+        if (!nslab || !nsym || !sym_first || !p->rec_first) return SPG_OUT_OF_MEMORY;
         launch(p, k_heavy_nslab, grid_for(p->nheavy, 256, sm * 8), 256, 0, hl, p->nheavy, p->win_lo, p->win_hi,
                p->nnzb, p->R, nslab, (long long *)(p->d_cnt + kCntNnzBHeavy));
-        TRY(scan_exclusive_i64(p, nslab, p->item_first, p->nheavy));
-        TRY(cuda_check(cudaMemcpyAsync(p->h_pinned, p->item_first + p->nheavy, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "items"));
-        TRY(cuda_check(cudaStreamSynchronize(st), "items"));
-        p->nitems = p->h_pinned[0];
-        p->item_col = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nitems);
-        p->item_slab = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nitems);
-        p->item_cnt = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nitems);
-        p->item_off = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)p->nitems);
-        p->hbits = (uint32_t *)ws_alloc(p, sizeof(uint32_t) * (size_t)p->nitems * (size_t)(p->R / 32));
+        TRY(scan_exclusive_i64(p, nslab, p->rec_first, p->nheavy));
+        TRY(cuda_check(cudaMemcpyAsync(p->h_pinned, p->rec_first + p->nheavy, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "records"));
+        TRY(cuda_check(cudaStreamSynchronize(st), "records"));
+        p->nrec = p->h_pinned[0];
+        if (p->nrec >= INT32_MAX) {
+            set_error("too many heavy slab records (%lld)", (long long)p->nrec);
+            return SPG_UNSUPPORTED;
+        }
+        p->rec_col = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nrec);
+        p->rec_slab = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nrec);
+        p->rec_cnt = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nrec);
+        p->rec_off = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)p->nrec);
+        p->hbits = (uint32_t *)ws_alloc(p, sizeof(uint32_t) * (size_t)p->nrec * (size_t)(p->R / 32));
         p->split = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->ndt + 1) * (size_t)(p->T + 1));
-        if (!p->item_col || !p->item_slab || !p->item_cnt || !p->item_off || !p->hbits || !p->split)
+        if (!p->rec_col || !p->rec_slab || !p->rec_cnt || !p->rec_off || !p->hbits || !p->split)
             return SPG_OUT_OF_MEMORY;
-        launch(p, k_heavy_items, grid_for(p->nheavy, 256, sm * 8), 256, 0, hl, p->nheavy, p->win_lo, p->R, p->item_first,
-                                                                        p->item_col, p->item_slab);
+        launch(p, k_heavy_records, grid_for(p->nheavy, 256, sm * 8), 256, 0, hl, p->nheavy, p->win_lo, p->R,
+               p->sym_max_recs, p->rec_first, p->rec_col, p->rec_slab, nsym);
+        TRY(scan_exclusive_i64(p, nsym, sym_first, p->nheavy));
+        TRY(cuda_check(cudaMemcpyAsync(p->h_pinned, sym_first + p->nheavy, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "items"));
+        TRY(cuda_check(cudaStreamSynchronize(st), "items"));
+        p->nsym = p->h_pinned[0];
+        p->sym_rec0 = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nsym);
+        p->sym_nrec = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)p->nsym);
+        if (!p->sym_rec0 || !p->sym_nrec) return SPG_OUT_OF_MEMORY;
+        launch(p, k_sym_items, grid_for(p->nheavy, 256, sm * 8), 256, 0, p->nheavy, p->sym_max_recs, p->rec_first,
+               sym_first, p->sym_rec0, p->sym_nrec);
         if (p->ndt > 0)
             launch(p, k_split, grid_for(p->ndt * (p->T + 1), 256, sm * 16), 256, 0, p->At_colptr, p->At_row, p->ndt, p->T,
                                                                                  p->R, p->split);
@@ -715,7 +769,7 @@ static spg_status plan_build(spg_plan *p) {
     S.empty_columns = p->bin_off[kBinEmpty + 1] - p->bin_off[kBinEmpty];
     S.heavy_columns = p->nheavy;
     S.light_columns = n - S.empty_columns - S.heavy_columns;
-    S.heavy_items = p->nitems;
+    S.heavy_items = p->nrec;
     S.nnzB_heavy = p->h_pinned[kCntNnzBHeavy];
     S.nnzC_heavy = -1;
     float ms = 0;
@@ -779,7 +833,7 @@ extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_
         return SPG_UNSUPPORTED;
     }
     int lm = opt->light_max ? opt->light_max : 1024;
-    int R = opt->slab_rows ? opt->slab_rows : 8192;
+    int R = opt->slab_rows ? opt->slab_rows : 4096;
     if (lm < 32 || lm > 1024 || (lm & (lm - 1)) || R < 1024 || R > 16384 || (R & (R - 1))) {
         set_error("light_max must be a power of two in [32, 1024] and slab_rows one in [1024, 16384]");
         return SPG_INVALID_ARGUMENT;
@@ -805,6 +859,9 @@ extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_
     p->out_idx64 = A->idx_type == SPG_IDX_I64;
     p->light_max = lm;
     p->R = R;
+    p->num_cap = R > 4096 ? R : 4096;  // one base slab always fits a numeric item
+    p->sym_max_recs = kSymMaxWords / (R / 32);
+    p->num_max_recs = kNumMaxWords / (R / 32);
     int dev = 0;
     spg_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
     if (!s) s = cuda_check(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev), "attr");

@@ -13,8 +13,9 @@
 //   flops, win_lo/hi, nnzb, maxa      per output column statistics (Section 3.2 flop count)
 //   binlist   n i32                   column ids grouped by bin
 //   split     sum|D~_i| * (T+1) i32   heavy bins only: offset of the first row >= t*R in each
-//                                     A~ column (R rows per slab, T = ceil(m/R))
-//   hbits     items * R/32 u32        heavy bins only: symbolic row bitmap of each (column, slab)
+//                                     A~ column (R rows per base slab, T = ceil(m/R))
+//   hbits     records * R/32 u32      heavy bins only: symbolic row bitmap of each
+//                                     (column, base slab) record
 #pragma once
 
 #include <cuda_runtime.h>
@@ -90,14 +91,24 @@ struct spg_plan {
     int64_t bin_off[spg::kNumBins + 1] = {0};
     int64_t *d_bincur = nullptr;
 
-    // heavy bins
-    int64_t nheavy = 0, nitems = 0;
+    // heavy bins.  A record is one (heavy column, base slab of R rows) inside
+    // the column's row window; the records of a column are consecutive.
+    int64_t nheavy = 0, nrec = 0;
     int32_t *split = nullptr;
-    int64_t *item_first = nullptr;  // per heavy column: first item (nheavy + 1)
-    int32_t *item_col = nullptr, *item_slab = nullptr;
-    int32_t *item_cnt = nullptr;
-    int64_t *item_off = nullptr;
-    uint32_t *hbits = nullptr;
+    int64_t *rec_first = nullptr;  // per heavy column: first record (nheavy + 1)
+    int32_t *rec_col = nullptr, *rec_slab = nullptr;
+    int32_t *rec_cnt = nullptr;    // nnz of C inside the record
+    int64_t *rec_off = nullptr;    // offset of the record inside its column of C
+    uint32_t *hbits = nullptr;     // R/32 words per record
+    // symbolic items: <= sym_max_recs consecutive records of one column
+    int64_t nsym = 0;
+    int32_t *sym_rec0 = nullptr, *sym_nrec = nullptr;
+    int sym_max_recs = 64;
+    // numeric items: <= num_max_recs consecutive records of one column holding
+    // <= num_cap entries of C
+    int64_t nnum = 0;
+    int32_t *num_rec0 = nullptr, *num_nrec = nullptr;
+    int num_cap = 4096, num_max_recs = 32;
 
     // symbolic / numeric
     int64_t *nnzcol = nullptr;
@@ -233,6 +244,14 @@ __device__ __forceinline__ void warp_products(int64_t p0, int64_t p1, int lane, 
         __syncwarp();
     }
 }
+
+// Heavy items: the rows of a symbolic item have their bitmap in shared memory
+// (at most kSymMaxWords words = 262,144 rows), those of a numeric item their
+// packed (bitmap word, prefix) pairs (at most kNumMaxWords = 131,072 rows).
+constexpr int kSymMaxWords = 8192;
+constexpr int kNumMaxWords = 4096;
+constexpr int kBatch = 256;   // B' entries staged per round by cta_products
+constexpr int kLongSeg = 32;  // segments this long are walked 32 entries per warp step
 
 __device__ __forceinline__ unsigned hash_row(int r, int shift) {
     return ((unsigned)r * 0x9E3779B1u) >> shift;

@@ -2,9 +2,11 @@
 // pointers of C (Algorithm 1, local multiply, first of its two passes).
 //   light bins: one warp per column, open-addressing table of 2^LOGS row ids
 //               in shared memory, sized >= 2 x min(flops_j, row window)
-//   heavy bin:  one CTA per (column, row slab of R rows): a shared bitmap of
-//               the slab; the bitmap is kept for the numeric pass, which uses
-//               it to place every product at its final rank without sorting
+//   heavy bin:  one CTA per item of up to 262,144 rows (base slabs) of a column:
+//               a shared bitmap of the item's rows; the per-slab bitmaps are
+//               kept for the numeric pass, which uses them to place every
+//               product at its final rank without sorting
+#include "cta_products.cuh"
 #include "spg_internal.cuh"
 
 namespace spg {
@@ -48,74 +50,108 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
+// One CTA per symbolic item: records [r0, r0 + nr) of one heavy column, i.e.
+// base slabs t0 .. t0 + nr - 1.  Every product sets its row's bit; then the
+// bitmap of each record and its population count are stored.
 __global__ void __launch_bounds__(256)
-    k_sym_heavy(int64_t nitems, const int32_t *__restrict__ item_col, const int32_t *__restrict__ item_slab,
-                const void *Bcolptr, int p64, const int32_t *__restrict__ Bq,
-                const int64_t *__restrict__ At_colptr, const int32_t *__restrict__ At_row,
-                const int32_t *__restrict__ split, int T, int R, uint32_t *__restrict__ hbits,
-                int32_t *__restrict__ item_cnt) {
+    k_sym_heavy(int64_t nitems, const int32_t *__restrict__ sym_rec0, const int32_t *__restrict__ sym_nrec,
+                const int32_t *__restrict__ rec_col, const int32_t *__restrict__ rec_slab, const void *Bcolptr,
+                int p64, const int32_t *__restrict__ Bq, const int64_t *__restrict__ At_colptr,
+                const int32_t *__restrict__ At_row, const int32_t *__restrict__ split, int T, int R,
+                uint32_t *__restrict__ hbits, int32_t *__restrict__ rec_cnt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RW = R >> 5;
-    WarpSeg<long long> *segs = (WarpSeg<long long> *)smem_raw;
-    uint32_t *bits = (uint32_t *)(segs + (blockDim.x >> 5));
-    __shared__ int red[33];
+    CtaBatch<long long> &sb = *(CtaBatch<long long> *)smem_raw;
+    uint32_t *bits = (uint32_t *)(smem_raw + sizeof(CtaBatch<long long>));
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int j = item_col[it], t = item_slab[it];
-        for (int w = threadIdx.x; w < RW; w += blockDim.x) bits[w] = 0;
+        const int r0 = sym_rec0[it], nr = sym_nrec[it];
+        const int j = rec_col[r0], t0 = rec_slab[r0];
+        const int nwords = nr * RW;
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) bits[w] = 0;
         __syncthreads();
         const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
-        const int64_t wbase = (int64_t)t * RW;
-        for (int64_t c0 = p0 + (int64_t)wid * 32; c0 < p1; c0 += (int64_t)nw * 32) {
-            warp_products<false, long long>(
-                c0, min(c0 + 32, p1), lane, segs[wid], At_row, (const long long *)nullptr,
-                [&](int64_t p, long long &st, int &len, long long &) {
-                    int q = Bq[p];
-                    if (q >= 0) {
-                        const int32_t *sp = split + (int64_t)q * (T + 1) + t;
-                        int a = sp[0], b = sp[1];
-                        st = At_colptr[q] + a;
-                        len = b - a;
-                    }
-                },
-                [&](int r, long long) { atomicOr(bits + ((r >> 5) - wbase), 1u << (r & 31)); });
-        }
-        __syncthreads();
-        int c = 0;
-        uint32_t *dst = hbits + it * RW;
-        for (int w = threadIdx.x; w < RW; w += blockDim.x) {
-            uint32_t x = bits[w];
-            dst[w] = x;
-            c += __popc(x);
-        }
-        c = warp_sum_i(c);
-        if (lane == 0) red[wid] = c;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int s = 0;
-            for (int w = 0; w < nw; w++) s += red[w];
-            item_cnt[it] = s;
+        const int wbase = t0 * RW;
+        cta_products<false, 4, long long>(
+            p0, p1, sb, At_row, (const long long *)nullptr,
+            [&](int64_t p, long long &st, int &len, long long &) {
+                int q = Bq[p];
+                if (q >= 0) {
+                    const int32_t *sp = split + (int64_t)q * (T + 1);
+                    int a = sp[t0], b = sp[t0 + nr];
+                    st = At_colptr[q] + a;
+                    len = b - a;
+                }
+            },
+            [&](int r, long long) { atomicOr(bits + ((r >> 5) - wbase), 1u << (r & 31)); });
+        // cta_products ends with a barrier: the bitmap is complete
+        uint32_t *dst = hbits + (int64_t)r0 * RW;
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) dst[w] = bits[w];
+        for (int rr = wid; rr < nr; rr += nw) {
+            int c = 0;
+            for (int w = lane; w < RW; w += 32) c += __popc(bits[rr * RW + w]);
+            c = warp_sum_i(c);
+            if (lane == 0) rec_cnt[r0 + rr] = c;
         }
         __syncthreads();
     }
 }
 
-// Per heavy column: place each slab after the ones above it, total = nnz_j.
-__global__ void k_heavy_offsets(const int32_t *list, int64_t nheavy, const int64_t *item_first,
-                                const int32_t *item_cnt, int64_t *item_off, int64_t *nnzcol,
-                                long long *nnzc_heavy) {
+// Per heavy column: offset of each record inside the column, nnz_j, and the
+// number of numeric items (greedy groups of consecutive records holding at
+// most `cap` entries and at most maxrec records).
+__device__ __forceinline__ int num_groups(const int32_t *rec_cnt, int64_t r0, int64_t r1, int cap, int maxrec,
+                                          int32_t *g_rec0, int32_t *g_nrec) {
+    int groups = 0, cur = 0, nin = 0;
+    int64_t start = r0;
+    for (int64_t r = r0; r < r1; r++) {
+        int c = rec_cnt[r];
+        if (nin > 0 && (cur + c > cap || nin == maxrec)) {
+            if (g_rec0) {
+                g_rec0[groups] = (int32_t)start;
+                g_nrec[groups] = nin;
+            }
+            groups++;
+            cur = 0;
+            nin = 0;
+            start = r;
+        }
+        cur += c;
+        nin++;
+    }
+    if (nin > 0) {
+        if (g_rec0) {
+            g_rec0[groups] = (int32_t)start;
+            g_nrec[groups] = nin;
+        }
+        groups++;
+    }
+    return groups;
+}
+
+__global__ void k_heavy_offsets(const int32_t *list, int64_t nheavy, const int64_t *rec_first,
+                                const int32_t *rec_cnt, int64_t *rec_off, int64_t *nnzcol, int cap, int maxrec,
+                                int64_t *nnum, long long *nnzc_heavy) {
     long long sum = 0;
     for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += (int64_t)gridDim.x * blockDim.x) {
         int64_t off = 0;
-        for (int64_t it = item_first[h]; it < item_first[h + 1]; it++) {
-            item_off[it] = off;
-            off += item_cnt[it];
+        for (int64_t r = rec_first[h]; r < rec_first[h + 1]; r++) {
+            rec_off[r] = off;
+            off += rec_cnt[r];
         }
         nnzcol[list[h]] = off;
+        nnum[h] = num_groups(rec_cnt, rec_first[h], rec_first[h + 1], cap, maxrec, nullptr, nullptr);
         sum += off;
     }
     sum = warp_sum_ll(sum);
     if ((threadIdx.x & 31) == 0 && sum) atomicAdd((unsigned long long *)nnzc_heavy, (unsigned long long)sum);
+}
+
+__global__ void k_num_items(int64_t nheavy, const int64_t *rec_first, const int32_t *rec_cnt, int cap, int maxrec,
+                            const int64_t *num_first, int32_t *num_rec0, int32_t *num_nrec) {
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += (int64_t)gridDim.x * blockDim.x)
+        num_groups(rec_cnt, rec_first[h], rec_first[h + 1], cap, maxrec, num_rec0 + num_first[h],
+                   num_nrec + num_first[h]);
 }
 
 template <int LOGS, int WARPS>
@@ -130,6 +166,43 @@ static spg_status launch_sym_light(spg_plan *p, const int32_t *list, int64_t cnt
     launch(p, kern, g, WARPS * 32, smem, list, cnt, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr,
            p->At_row, p->nnzcol, p->d_err);
     return cuda_check(cudaGetLastError(), "symbolic light");
+}
+
+static spg_status symbolic_heavy(spg_plan *p) {
+    cudaStream_t st = p->st;
+    const int threads = 256;
+    size_t smem = sizeof(CtaBatch<long long>) + sizeof(uint32_t) * (size_t)kSymMaxWords;
+    cudaFuncSetAttribute(k_sym_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sym_heavy, threads, smem);
+    if (occ < 1) occ = 1;
+    int g = grid_for(p->nsym, 1, p->sm_count * occ);
+    group_begin(p, kKSymHeavy);
+    launch(p, k_sym_heavy, g, threads, smem, p->nsym, p->sym_rec0, p->sym_nrec, p->rec_col, p->rec_slab,
+           p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr, p->At_row, p->split, p->T, p->R,
+           p->hbits, p->rec_cnt);
+    group_end(p, kKSymHeavy);
+    int64_t *nnum = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
+    int64_t *num_first = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
+    if (!nnum || !num_first) return SPG_OUT_OF_MEMORY;
+    const int gh = grid_for(p->nheavy, 256, p->sm_count * 8);
+    launch(p, k_heavy_offsets, gh, 256, 0, p->binlist + p->bin_off[kBinHeavy], p->nheavy, p->rec_first, p->rec_cnt,
+           p->rec_off, p->nnzcol, p->num_cap, p->num_max_recs, nnum, (long long *)(p->d_cnt + kCntNnzCHeavySlot));
+    spg_status s = scan_exclusive_i64(p, nnum, num_first, p->nheavy);
+    if (s) return s;
+    s = cuda_check(cudaMemcpyAsync(p->h_pinned + 2, num_first + p->nheavy, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+                   "numeric items");
+    if (s) return s;
+    s = cuda_check(cudaStreamSynchronize(st), "numeric items");
+    if (s) return s;
+    p->nnum = p->h_pinned[2];
+    p->num_rec0 = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->nnum + 1));
+    p->num_nrec = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->nnum + 1));
+    if (!p->num_rec0 || !p->num_nrec) return SPG_OUT_OF_MEMORY;
+    launch(p, k_num_items, gh, 256, 0, p->nheavy, p->rec_first, p->rec_cnt, p->num_cap, p->num_max_recs, num_first,
+           p->num_rec0,
+           p->num_nrec);
+    return cuda_check(cudaGetLastError(), "symbolic heavy");
 }
 
 spg_status run_symbolic(spg_plan *p) {
@@ -156,23 +229,8 @@ spg_status run_symbolic(spg_plan *p) {
     }
     if (p->bin_off[kMaxLightBin + 1] > p->bin_off[1]) group_end(p, kKSymLight);
     if (s) return s;
-    if (p->nitems > 0) {
-        const int threads = 256;
-        size_t smem = sizeof(WarpSeg<long long>) * (threads / 32) + sizeof(uint32_t) * (size_t)(p->R / 32);
-        cudaFuncSetAttribute(k_sym_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int occ = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sym_heavy, threads, smem);
-        if (occ < 1) occ = 1;
-        int g = grid_for(p->nitems, 1, p->sm_count * occ);
-        group_begin(p, kKSymHeavy);
-        launch(p, k_sym_heavy, g, threads, smem, p->nitems, p->item_col, p->item_slab, p->B.colptr,
-               p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr, p->At_row, p->split, p->T, p->R, p->hbits,
-               p->item_cnt);
-        group_end(p, kKSymHeavy);
-        launch(p, k_heavy_offsets, grid_for(p->nheavy, 256, p->sm_count * 8), 256, 0,
-               p->binlist + p->bin_off[kBinHeavy], p->nheavy, p->item_first, p->item_cnt, p->item_off, p->nnzcol,
-               (long long *)(p->d_cnt + kCntNnzCHeavySlot));
-        s = cuda_check(cudaGetLastError(), "symbolic heavy");
+    if (p->nrec > 0) {
+        s = symbolic_heavy(p);
         if (s) return s;
     }
     s = scan_exclusive_i64(p, p->nnzcol, p->Ccolptr, n);
