@@ -192,6 +192,28 @@ spg_status spgemm_plan_export(const spg_plan *plan, int32_t block, void *H_bits,
                               int64_t *n_dtilde, void *fetch, void *At_colptr, void *At_rowidx,
                               void *At_vals, void *flops);
 
+/*
+ * nnz(C(:,j)) for every column j of C = A * B, written to nnz_out (device,
+ * B.ncols int64 entries, caller-allocated), without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory at all -- a process whose GPU memory is owned
+ * entirely by another allocator, a service that reserves its memory once at
+ * start-up, or a latency path where an allocation call (which can synchronise
+ * the device) is not acceptable.  Its scratch is one fixed array inside the
+ * library (8 MiB, held on every GPU that loads the library until the process
+ * exits), so:
+ *   - A may have at most 1,048,576 rows (SPG_UNSUPPORTED otherwise);
+ *   - calls whose kernels overlap on the GPU share that array and race:
+ *     order them on one stream;
+ *   - the first call on a device looks up the array's address with that
+ *     device current (cudaGetSymbolAddress); make that first call before any
+ *     stream capture on the device.
+ * Inputs must be canonical (no validation pass: that would need memory for a
+ * flag).  Asynchronous on `stream` (a cudaStream_t; NULL = legacy stream).
+ * Errors: SPG_INVALID_ARGUMENT, SPG_UNSUPPORTED, SPG_CUDA_ERROR.
+ */
+spg_status spgemm_count_noalloc(const spg_csc *A, const spg_csc *B, int64_t *nnz_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,8 +95,10 @@ def load_library(path: str = LIB_PATH):
             lib.spgemm_plan_destroy.argtypes = [vp]
             lib.spgemm_last_error.restype = ctypes.c_char_p
             lib.spgemm_plan_export.argtypes = [vp, i32, vp, vp, ctypes.POINTER(i64), vp, vp, vp, vp, vp]
+            lib.spgemm_count_noalloc.argtypes = [ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc), vp, vp]
             for name in ("spgemm_plan", "spgemm_symbolic", "spgemm_numeric", "spgemm_1d_multiply",
-                         "spgemm_plan_stats", "spgemm_plan_destroy", "spgemm_plan_export"):
+                         "spgemm_plan_stats", "spgemm_plan_destroy", "spgemm_plan_export",
+                         "spgemm_count_noalloc"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -338,3 +340,21 @@ def multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, **kw) -> DeviceCSC:
         return spgemm_numeric(plan)
     finally:
         spgemm_plan_destroy(plan)
+
+
+def spgemm_count_noalloc(A: DeviceCSC, B: DeviceCSC, nnz_out: torch.Tensor | None = None, stream=None):
+    """nnz(C(:,j)) of C = A*B through the entry point that allocates nothing.
+
+    For callers that may not allocate device memory: the library keeps its
+    scratch in one fixed 8 MiB array per GPU, so A may have at most 1,048,576
+    rows, and calls that overlap on the GPU race (order them on one stream).
+    The output array is the caller's (allocated here by torch if not given)."""
+    lib = load_library()
+    if nnz_out is None:
+        nnz_out = torch.empty(max(B.ncols, 1), dtype=torch.int64, device=B.colptr.device)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    a, b = A.as_c(), B.as_c()
+    _check(lib.spgemm_count_noalloc(ctypes.byref(a), ctypes.byref(b), nnz_out.data_ptr(),
+                                    ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))))
+    return nnz_out[: B.ncols]
