@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256)
         const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
         const int wbase = t0 * RW;
         bool miss = false;
-        cta_products<true, 2, Acc>(
+        cta_products<true, SPG_NUM_UNROLL, Acc>(
             p0, p1, sb, At_row, At_val,
             [&](int64_t p, long long &st, int &len, Acc &bv) {
                 int q = Bq[p];

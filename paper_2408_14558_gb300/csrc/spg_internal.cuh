@@ -250,6 +250,14 @@ __device__ __forceinline__ void warp_products(int64_t p0, int64_t p1, int lane, 
 // packed (bitmap word, prefix) pairs (at most kNumMaxWords = 131,072 rows).
 constexpr int kSymMaxWords = 8192;
 constexpr int kNumMaxWords = 4096;
+// Chunks of 32 products each warp keeps in flight in the heavy kernels
+// (compile-time tuning knobs).
+#ifndef SPG_NUM_UNROLL
+#define SPG_NUM_UNROLL 4
+#endif
+#ifndef SPG_SYM_UNROLL
+#define SPG_SYM_UNROLL 8
+#endif
 constexpr int kBatch = 256;   // B' entries staged per round by cta_products
 constexpr int kLongSeg = 32;  // segments this long are walked 32 entries per warp step
 

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
         const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
         const int wbase = t0 * RW;
-        cta_products<false, 4, long long>(
+        cta_products<false, SPG_SYM_UNROLL, long long>(
             p0, p1, sb, At_row, (const long long *)nullptr,
             [&](int64_t p, long long &st, int &len, long long &) {
                 int q = Bq[p];
