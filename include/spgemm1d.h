@@ -116,6 +116,7 @@ typedef struct {
     int64_t nnzB_heavy;          /* nonzeros of B in the heavy (dense-slab) columns */
     int64_t nnzC_heavy;          /* nonzeros of C in the heavy columns (-1 before symbolic) */
     int64_t kernel_launches;     /* kernels this plan launched so far */
+    int64_t learned_capacity;    /* learned sizing: sum of the predicted column capacities (0 otherwise) */
     double ms_plan, ms_symbolic, ms_numeric; /* device time of each phase (CUDA events) */
     /* device time of kernel groups (CUDA events on the plan's stream):
      * gather = A~ copy; sym/num light = all warp-hash bins; sym/num heavy = dense slabs */
@@ -170,6 +171,11 @@ spg_status spgemm_1d_multiply(const spg_csc *A, const spg_csc *B, const spg_opti
 /* Copy the plan's counters into *st (host).  Synchronises the stream. */
 spg_status spgemm_plan_stats(const spg_plan *plan, spg_stats *st);
 
+/* Counters of the last successful spgemm_1d_multiply on the calling thread
+ * (its plan is gone by then; this keeps a copy).  SPG_INVALID_ARGUMENT if
+ * there was none. */
+spg_status spgemm_last_multiply_stats(spg_stats *st);
+
 /* Release the plan and its workspace (stream-ordered).  NULL is a no-op. */
 spg_status spgemm_plan_destroy(spg_plan *plan);
 
@@ -191,6 +197,48 @@ const char *spgemm_last_error(void);
 spg_status spgemm_plan_export(const spg_plan *plan, int32_t block, void *H_bits, void *dtilde,
                               int64_t *n_dtilde, void *fetch, void *At_colptr, void *At_rowidx,
                               void *At_vals, void *flops);
+
+/* ---------------------------------------------------------------------------
+ * Learned nnz sizing (an extension beyond the paper).  A small float32 MLP
+ * (4 inputs, two hidden layers of 32 ReLU units, one output) predicts
+ * log1p(nnz(C(:,j))) from log1p of four features of column j: flops_j,
+ * nnz(B(:,j)), and the largest and mean nnz(A(:,k)) over the k of B(:,j).
+ * With spg_options.sizing = SPG_SIZING_LEARNED and .model set,
+ * spgemm_1d_multiply sizes every column's output room from the prediction
+ * (times learned_slack, at most the exact bound min(flops_j, row window)),
+ * runs the numeric work without the symbolic pass and recomputes the columns
+ * that overflow through the exact path; C is the exact path's C.
+ * Parameters: one flat float vector of SPG_MODEL_NPARAMS entries, laid out
+ * W1 (32 x 4, row-major by hidden unit) | b1 (32) | W2 (32 x 32) | b2 (32) |
+ * w3 (32) | b3 (1).  X arrays are n x 4 row-major device floats; y, out are
+ * n device floats.  All device work runs on `stream`.
+ * ------------------------------------------------------------------------ */
+#define SPG_MODEL_NPARAMS 1249
+typedef struct spg_model spg_model;
+
+/* He-normal weights from `seed` (splitmix64 + Box-Muller), zero biases. */
+spg_status spgemm_model_create(uint64_t seed, spg_model **out);
+spg_status spgemm_model_destroy(spg_model *model);
+/* Host copies of the parameters; set also resets the Adam state. */
+spg_status spgemm_model_set_params(spg_model *model, const float *params, int64_t count);
+spg_status spgemm_model_get_params(const spg_model *model, float *params, int64_t count);
+/* epochs over the n samples in mini-batches of `batch` (in order), one Adam
+ * step (beta 0.9 / 0.999, eps 1e-8) per batch; *final_loss (host, may be NULL)
+ * receives the mean squared error over all samples afterwards.  Synchronises. */
+spg_status spgemm_model_train(spg_model *model, const float *X, const float *y, int64_t n, int32_t epochs,
+                              int32_t batch, float lr, void *stream, float *final_loss);
+spg_status spgemm_model_predict(const spg_model *model, const float *X, int64_t n, float *out, void *stream);
+/* Gradient of the mean squared error over the n samples (host, NPARAMS
+ * floats) and the loss; no parameter changes.  Synchronises. */
+spg_status spgemm_model_gradient(spg_model *model, const float *X, const float *y, int64_t n, float *grad,
+                                 float *loss, void *stream);
+/* Binary file: "SPGMLP01", int32 count, count float32 parameters. */
+spg_status spgemm_model_save(const spg_model *model, const char *path);
+spg_status spgemm_model_load(const char *path, spg_model **out);
+/* Training data from a plan: features X (n x 4) of every output column, and
+ * after spgemm_symbolic the labels y = log1p(nnz(C(:,j))). */
+spg_status spgemm_plan_features(const spg_plan *plan, float *X);
+spg_status spgemm_plan_labels(const spg_plan *plan, float *y);
 
 /*
  * nnz(C(:,j)) for every column j of C = A * B, written to nnz_out (device,

@@ -65,7 +65,7 @@ class spg_stats(ctypes.Structure):
         "m", "k", "n", "nnzA", "nnzB", "P", "b", "products", "nnzC", "sum_H", "sum_dtilde",
         "fetch_blocks_total", "fetch_blocks_chosen", "gathered_nnz_exact", "gathered_nnz_block",
         "light_columns", "heavy_columns", "heavy_items", "empty_columns", "recomputed_columns",
-        "nnzB_heavy", "nnzC_heavy", "kernel_launches")] + [
+        "nnzB_heavy", "nnzC_heavy", "kernel_launches", "learned_capacity")] + [
         (name, ctypes.c_double) for name in ("ms_plan", "ms_symbolic", "ms_numeric", "ms_gather", "ms_sym_light",
                                              "ms_sym_heavy", "ms_num_light", "ms_num_heavy")]
 
@@ -277,6 +277,16 @@ def spgemm_plan_stats(plan: Plan) -> dict:
     return {name: getattr(st, name) for name, _ in spg_stats._fields_}
 
 
+def spgemm_last_multiply_stats() -> dict:
+    """Counters of the last spgemm_1d_multiply on this thread."""
+    lib = load_library()
+    lib.spgemm_last_multiply_stats.argtypes = [ctypes.POINTER(spg_stats)]
+    lib.spgemm_last_multiply_stats.restype = ctypes.c_int
+    st = spg_stats()
+    _check(lib.spgemm_last_multiply_stats(ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in spg_stats._fields_}
+
+
 def spgemm_plan_destroy(plan: Plan):
     if plan.handle:
         _check(load_library().spgemm_plan_destroy(plan.handle))
@@ -358,3 +368,125 @@ def spgemm_count_noalloc(A: DeviceCSC, B: DeviceCSC, nnz_out: torch.Tensor | Non
     _check(lib.spgemm_count_noalloc(ctypes.byref(a), ctypes.byref(b), nnz_out.data_ptr(),
                                     ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))))
     return nnz_out[: B.ncols]
+
+
+# ------------------------------------------------------ learned nnz sizing
+
+SPG_MODEL_NPARAMS = 1249
+
+
+class Model:
+    """Handle of an spg_model (the nnz-prediction MLP, parameters on the GPU)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                load_library().spgemm_model_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def _model_lib():
+    lib = load_library()
+    if not getattr(lib, "_model_ready", False):
+        vp, i64, i32, f32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.spgemm_model_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(vp)]
+        lib.spgemm_model_destroy.argtypes = [vp]
+        lib.spgemm_model_set_params.argtypes = [vp, fp, i64]
+        lib.spgemm_model_get_params.argtypes = [vp, fp, i64]
+        lib.spgemm_model_train.argtypes = [vp, vp, vp, i64, i32, i32, f32, vp, fp]
+        lib.spgemm_model_predict.argtypes = [vp, vp, i64, vp, vp]
+        lib.spgemm_model_gradient.argtypes = [vp, vp, vp, i64, fp, fp, vp]
+        lib.spgemm_model_save.argtypes = [vp, ctypes.c_char_p]
+        lib.spgemm_model_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
+        lib.spgemm_plan_features.argtypes = [vp, vp]
+        lib.spgemm_plan_labels.argtypes = [vp, vp]
+        for name in ("spgemm_model_create", "spgemm_model_destroy", "spgemm_model_set_params",
+                     "spgemm_model_get_params", "spgemm_model_train", "spgemm_model_predict",
+                     "spgemm_model_gradient", "spgemm_model_save", "spgemm_model_load",
+                     "spgemm_plan_features", "spgemm_plan_labels"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib._model_ready = True
+    return lib
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def spgemm_model_create(seed: int = 0) -> Model:
+    h = ctypes.c_void_p()
+    _check(_model_lib().spgemm_model_create(ctypes.c_uint64(seed), ctypes.byref(h)))
+    return Model(h)
+
+
+def spgemm_model_load(path: str) -> Model:
+    h = ctypes.c_void_p()
+    _check(_model_lib().spgemm_model_load(path.encode(), ctypes.byref(h)))
+    return Model(h)
+
+
+def spgemm_model_save(model: Model, path: str):
+    _check(_model_lib().spgemm_model_save(model.handle, path.encode()))
+
+
+def spgemm_model_get_params(model: Model):
+    import numpy as np
+    out = np.zeros(SPG_MODEL_NPARAMS, dtype=np.float32)
+    _check(_model_lib().spgemm_model_get_params(model.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                SPG_MODEL_NPARAMS))
+    return out
+
+
+def spgemm_model_set_params(model: Model, params):
+    import numpy as np
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_model_lib().spgemm_model_set_params(model.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+
+
+def spgemm_model_train(model: Model, X: torch.Tensor, y: torch.Tensor, epochs=10, batch=4096, lr=1e-3, stream=None):
+    """Train in place on device tensors X (n, 4) and y (n,); returns the final MSE."""
+    loss = ctypes.c_float()
+    X, y = X.contiguous().float(), y.contiguous().float()
+    _check(_model_lib().spgemm_model_train(model.handle, X.data_ptr(), y.data_ptr(), y.numel(), int(epochs),
+                                           int(batch), float(lr), _stream_ptr(stream), ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def spgemm_model_predict(model: Model, X: torch.Tensor, stream=None) -> torch.Tensor:
+    X = X.contiguous().float()
+    out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _check(_model_lib().spgemm_model_predict(model.handle, X.data_ptr(), X.shape[0], out.data_ptr(),
+                                             _stream_ptr(stream)))
+    return out
+
+
+def spgemm_model_gradient(model: Model, X: torch.Tensor, y: torch.Tensor, stream=None):
+    """(gradient of the MSE as a float32 numpy vector, loss)."""
+    import numpy as np
+    g = np.zeros(SPG_MODEL_NPARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    X, y = X.contiguous().float(), y.contiguous().float()
+    _check(_model_lib().spgemm_model_gradient(model.handle, X.data_ptr(), y.data_ptr(), y.numel(),
+                                              g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss),
+                                              _stream_ptr(stream)))
+    return g, float(loss.value)
+
+
+def spgemm_plan_features(plan: Plan) -> torch.Tensor:
+    X = torch.empty((max(plan.B.ncols, 1), 4), dtype=torch.float32, device=plan.B.colptr.device)
+    _check(_model_lib().spgemm_plan_features(plan.handle, X.data_ptr()))
+    return X[: plan.B.ncols]
+
+
+def spgemm_plan_labels(plan: Plan) -> torch.Tensor:
+    y = torch.empty(max(plan.B.ncols, 1), dtype=torch.float32, device=plan.B.colptr.device)
+    _check(_model_lib().spgemm_plan_labels(plan.handle, y.data_ptr()))
+    return y[: plan.B.ncols]

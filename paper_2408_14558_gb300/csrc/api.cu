@@ -13,6 +13,25 @@ using namespace spg;
 
 extern "C" const char *spgemm_last_error(void) { return last_error_str(); }
 
+static thread_local spg_stats g_last_stats;
+static thread_local bool g_have_last_stats = false;
+
+namespace spg {
+void remember_multiply_stats(const spg_stats &st) {
+    g_last_stats = st;
+    g_have_last_stats = true;
+}
+}  // namespace spg
+
+extern "C" spg_status spgemm_last_multiply_stats(spg_stats *st) {
+    if (!st || !g_have_last_stats) {
+        set_error("no spgemm_1d_multiply has completed on this thread");
+        return SPG_INVALID_ARGUMENT;
+    }
+    *st = g_last_stats;
+    return SPG_OK;
+}
+
 extern "C" spg_status spgemm_symbolic(spg_plan *p, void *C_colptr, int64_t *nnzC) {
     clear_error();
     if (!p || !nnzC) {
@@ -103,8 +122,6 @@ static void *alloc_user(const spg_options *opt, size_t bytes) {
     return p;
 }
 
-spg_status multiply_learned(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C);
-
 extern "C" spg_status spgemm_1d_multiply(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C) {
     clear_error();
     if (!C || !opt) {
@@ -146,6 +163,8 @@ extern "C" spg_status spgemm_1d_multiply(const spg_csc *A, const spg_csc *B, con
         set_error("%s", keep.c_str());
         return s;
     }
+    spg_stats st{};
+    if (spgemm_plan_stats(p, &st) == SPG_OK) remember_multiply_stats(st);
     spgemm_plan_destroy(p);
     return SPG_OK;
 }
@@ -197,9 +216,4 @@ extern "C" spg_status spgemm_plan_export(const spg_plan *pc, int32_t block, void
     }
     if (!s) s = cuda_check(cudaStreamSynchronize(st), "export");
     return s;
-}
-
-spg_status multiply_learned(const spg_csc *, const spg_csc *, const spg_options *, spg_csc *) {
-    set_error("learned sizing is not available in this build");
-    return SPG_UNSUPPORTED;
 }

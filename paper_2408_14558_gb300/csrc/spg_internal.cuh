@@ -167,6 +167,13 @@ spg_status bin_columns(spg_plan *p, const int8_t *bin_of, int32_t *list, int64_t
 // ---- phases
 spg_status run_symbolic(spg_plan *p);
 spg_status run_numeric(spg_plan *p, spg_csc *C);
+spg_status multiply_learned(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C);
+void remember_multiply_stats(const spg_stats &st);  // api.cu: spgemm_last_multiply_stats
+
+// ---- shared kernels (plan.cu): groups of <= smr consecutive records of every
+// heavy column, listed as (first record, count) starting at sym_first[h].
+__global__ void k_sym_items(int64_t nheavy, int smr, const int64_t *rec_first, const int64_t *sym_first,
+                            int32_t *sym_rec0, int32_t *sym_nrec);
 
 // ---- device helpers
 __device__ __forceinline__ int64_t ld_ptr(const void *p, int is64, int64_t i) {

@@ -95,15 +95,25 @@ def _distinct_rows(rng, d_per_col: np.ndarray, sampler, max_rounds=500):
     ncols = d_per_col.shape[0]
     cols = np.repeat(np.arange(ncols, dtype=np.int64), d_per_col)
     rows = sampler(cols.shape[0])
+    order = np.lexsort((rows, cols))
+    cols, rows = cols[order], rows[order]
+    # Entries of the columns still holding a repeat, as positions in the
+    # (col, row)-sorted arrays; a column's entries are contiguous, so re-sorting
+    # only those entries keeps the whole array sorted.
+    idx = np.arange(cols.shape[0])
     for _ in range(max_rounds):
-        order = np.lexsort((rows, cols))
-        cols, rows = cols[order], rows[order]
-        dup = np.zeros(cols.shape[0], dtype=bool)
-        dup[1:] = (cols[1:] == cols[:-1]) & (rows[1:] == rows[:-1])
+        c, r = cols[idx], rows[idx]
+        dup = np.zeros(idx.shape[0], dtype=bool)
+        dup[1:] = (c[1:] == c[:-1]) & (r[1:] == r[:-1])
         nd = int(dup.sum())
         if nd == 0:
             return cols, rows
-        rows[dup] = sampler(nd)
+        r = r.copy()
+        r[dup] = sampler(nd)
+        bad = np.isin(c, np.unique(c[dup]))
+        idx, c, r = idx[bad], c[bad], r[bad]
+        o = np.lexsort((r, c))
+        rows[idx] = r[o]
     raise RuntimeError("could not draw distinct rows")
 
 
