@@ -199,6 +199,66 @@ spg_status spgemm_plan_export(const spg_plan *plan, int32_t block, void *H_bits,
                               void *At_vals, void *flops);
 
 /* ---------------------------------------------------------------------------
+ * Batched execution (an extension beyond the paper): many independent
+ * products C_i = A_i * B_i, each one column block (P = 1), computed by one
+ * persistent kernel captured once in a CUDA graph and fed by a device work
+ * queue (symbolic tasks of every instance first, then numeric tasks; a
+ * numeric task waits, bounded by timeout_ns, for its instance's column
+ * pointers).  Limits: int32 row ids; every column of every C_i with at most
+ * 1024 products-bound entries (min(flops_j, m_i) <= 1024, SPG_UNSUPPORTED
+ * otherwise: use spgemm_1d_multiply); one value kind for all instances.
+ * The output of all instances lives in one pool owned by the batch, sized
+ * from per-instance bounds sum_j min(flops_j, m_i); the inputs must stay
+ * valid and unchanged while the batch exists.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t task_cols;      /* columns per queue task (>= 1; default 64) */
+    int32_t warps_per_cta;  /* 4 or 8 (default 8) */
+    int64_t timeout_ns;     /* bound of a numeric task's wait (default 2 s) */
+    int32_t stall_instance; /* failure test: numeric tasks of this instance wait on a flag nothing sets (-1 = off) */
+    int32_t reserved;
+} spg_batch_options;
+
+typedef struct spg_batch spg_batch;
+
+void spgemm_batch_default_options(spg_batch_options *opt);
+/* Plan the batch: task table, output bounds (one synchronising bounds pass),
+ * pools, and the captured graph.  A and B are arrays of `count` matrices. */
+spg_status spgemm_batch_create(int32_t count, const spg_csc *A, const spg_csc *B, const spg_batch_options *opt,
+                               spg_batch **out);
+/* Launch the batch's graph on `stream` (asynchronous). */
+spg_status spgemm_batch_execute(spg_batch *batch, void *stream);
+/* Synchronise `stream` and report the last execution: SPG_OK, SPG_TIMEOUT
+ * (a wait gave up) or SPG_CUDA_ERROR (a consistency check failed). */
+spg_status spgemm_batch_status(spg_batch *batch, void *stream);
+/* View of instance i's C inside the batch's pools (int64 colptr, int32 rows;
+ * device pointers owned by the batch).  Synchronous (reads nnz). */
+spg_status spgemm_batch_result(const spg_batch *batch, int32_t i, spg_csc *C);
+/* Copy instance i's C (colptr n+1 int64, rows int32, values 8 bytes) into
+ * caller device buffers, ordered on `stream`.  Any pointer may be NULL. */
+spg_status spgemm_batch_copy_result(const spg_batch *batch, int32_t i, void *colptr, void *rowidx, void *vals,
+                                    void *stream);
+/* Queue tasks (symbolic and numeric each), pool entries and persistent grid size. */
+spg_status spgemm_batch_info(const spg_batch *batch, int64_t *ntasks, int64_t *pool_entries, int32_t *grid);
+spg_status spgemm_batch_destroy(spg_batch *batch);
+
+/* ---------------------------------------------------------------------------
+ * Autotuner (an extension beyond the paper): times candidate configurations
+ * on the given inputs and returns the fastest; with cache_path (a JSON file,
+ * created or updated) the result is stored under the device name and a
+ * signature of the workload and reused without timing next time.
+ *   spgemm_batch_autotune: task_cols in {16, 64, 256} x warps_per_cta in
+ *     {4, 8}, timed on the first `sample` instances (0 = all).
+ *   spgemm_autotune: light_max in {256, 512, 1024} x slab_rows in
+ *     {2048, 4096, 8192} for the plain path (other fields from `base`).
+ * Both synchronise; best_ms (may be NULL) receives the winner's time.
+ * ------------------------------------------------------------------------ */
+spg_status spgemm_batch_autotune(int32_t count, const spg_csc *A, const spg_csc *B, int32_t sample,
+                                 const char *cache_path, spg_batch_options *best, double *best_ms);
+spg_status spgemm_autotune(const spg_csc *A, const spg_csc *B, const spg_options *base, const char *cache_path,
+                           spg_options *best, double *best_ms);
+
+/* ---------------------------------------------------------------------------
  * Learned nnz sizing (an extension beyond the paper).  A small float32 MLP
  * (4 inputs, two hidden layers of 32 ReLU units, one output) predicts
  * log1p(nnz(C(:,j))) from log1p of four features of column j: flops_j,

@@ -490,3 +490,132 @@ def spgemm_plan_labels(plan: Plan) -> torch.Tensor:
     y = torch.empty(max(plan.B.ncols, 1), dtype=torch.float32, device=plan.B.colptr.device)
     _check(_model_lib().spgemm_plan_labels(plan.handle, y.data_ptr()))
     return y[: plan.B.ncols]
+
+
+# --------------------------------------------------------- batched products
+
+class spg_batch_options(ctypes.Structure):
+    _fields_ = [("task_cols", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
+                ("stall_instance", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def _batch_lib():
+    lib = load_library()
+    if not getattr(lib, "_batch_ready", False):
+        vp = ctypes.c_void_p
+        lib.spgemm_batch_default_options.argtypes = [ctypes.POINTER(spg_batch_options)]
+        lib.spgemm_batch_default_options.restype = None
+        lib.spgemm_batch_create.argtypes = [ctypes.c_int32, ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc),
+                                            ctypes.POINTER(spg_batch_options), ctypes.POINTER(vp)]
+        lib.spgemm_batch_execute.argtypes = [vp, vp]
+        lib.spgemm_batch_status.argtypes = [vp, vp]
+        lib.spgemm_batch_result.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(spg_csc)]
+        lib.spgemm_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int32)]
+        lib.spgemm_batch_destroy.argtypes = [vp]
+        for name in ("spgemm_batch_create", "spgemm_batch_execute", "spgemm_batch_status", "spgemm_batch_result",
+                     "spgemm_batch_info", "spgemm_batch_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib._batch_ready = True
+    return lib
+
+
+class Batch:
+    """Handle of an spg_batch; keeps its inputs alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                load_library().spgemm_batch_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def spgemm_batch_create(As, Bs, task_cols=64, warps_per_cta=8, timeout_ns=2_000_000_000, stall_instance=-1) -> Batch:
+    lib = _batch_lib()
+    n = len(As)
+    a = (spg_csc * n)(*[X.as_c() for X in As])
+    b = (spg_csc * n)(*[X.as_c() for X in Bs])
+    o = spg_batch_options()
+    lib.spgemm_batch_default_options(ctypes.byref(o))
+    o.task_cols, o.warps_per_cta, o.timeout_ns, o.stall_instance = task_cols, warps_per_cta, timeout_ns, stall_instance
+    h = ctypes.c_void_p()
+    _check(lib.spgemm_batch_create(n, a, b, ctypes.byref(o), ctypes.byref(h)))
+    return Batch(h, (list(As), list(Bs)))
+
+
+def spgemm_batch_execute(batch: Batch, stream=None):
+    _check(_batch_lib().spgemm_batch_execute(batch.handle, _stream_ptr(stream)))
+
+
+def spgemm_batch_status(batch: Batch, stream=None) -> int:
+    """Synchronise and return the status of the last execution (raises on error)."""
+    return _check(_batch_lib().spgemm_batch_status(batch.handle, _stream_ptr(stream)))
+
+
+def spgemm_batch_result(batch: Batch, i: int):
+    """(colptr, rowidx, vals) of instance i as CUDA tensors (copies)."""
+    lib = _batch_lib()
+    c = spg_csc()
+    _check(lib.spgemm_batch_result(batch.handle, i, ctypes.byref(c)))
+    dev = batch._keep[0][i].colptr.device
+    val_dt = torch.float64 if c.val_type == SPG_VAL_F64 else torch.int64
+    colptr = torch.empty(c.ncols + 1, dtype=torch.int64, device=dev)
+    rowidx = torch.empty(max(c.nnz, 1), dtype=torch.int32, device=dev)
+    vals = torch.empty(max(c.nnz, 1), dtype=val_dt, device=dev)
+    lib.spgemm_batch_copy_result.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p]
+    lib.spgemm_batch_copy_result.restype = ctypes.c_int
+    _check(lib.spgemm_batch_copy_result(batch.handle, i, colptr.data_ptr(), rowidx.data_ptr(), vals.data_ptr(),
+                                        _stream_ptr(None)))
+    return colptr, rowidx[: c.nnz], vals[: c.nnz]
+
+
+def spgemm_batch_info(batch: Batch):
+    nt, pool, grid = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(_batch_lib().spgemm_batch_info(batch.handle, ctypes.byref(nt), ctypes.byref(pool), ctypes.byref(grid)))
+    return {"tasks": nt.value, "pool_entries": pool.value, "grid": grid.value}
+
+
+def spgemm_batch_autotune(As, Bs, sample=0, cache_path=None) -> dict:
+    """Fastest (task_cols, warps_per_cta) for this batch (cached in cache_path)."""
+    lib = _batch_lib()
+    lib.spgemm_batch_autotune.argtypes = [ctypes.c_int32, ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc),
+                                          ctypes.c_int32, ctypes.c_char_p, ctypes.POINTER(spg_batch_options),
+                                          ctypes.POINTER(ctypes.c_double)]
+    lib.spgemm_batch_autotune.restype = ctypes.c_int
+    n = len(As)
+    a = (spg_csc * n)(*[X.as_c() for X in As])
+    b = (spg_csc * n)(*[X.as_c() for X in Bs])
+    o = spg_batch_options()
+    ms = ctypes.c_double()
+    _check(lib.spgemm_batch_autotune(n, a, b, int(sample), cache_path.encode() if cache_path else None,
+                                     ctypes.byref(o), ctypes.byref(ms)))
+    return {"task_cols": o.task_cols, "warps_per_cta": o.warps_per_cta, "ms": ms.value}
+
+
+def spgemm_autotune(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, cache_path=None, stream=None) -> dict:
+    """Fastest (light_max, slab_rows) of the plain path for A*B (cached in cache_path)."""
+    lib = load_library()
+    lib.spgemm_autotune.argtypes = [ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc), ctypes.POINTER(spg_options),
+                                    ctypes.c_char_p, ctypes.POINTER(spg_options), ctypes.POINTER(ctypes.c_double)]
+    lib.spgemm_autotune.restype = ctypes.c_int
+    alloc = _TorchAllocator(A.colptr.device)
+    base = make_options(P, b, stream, True, allocator=alloc)
+    best = spg_options()
+    ms = ctypes.c_double()
+    a, bb = A.as_c(), B.as_c()
+    _check(lib.spgemm_autotune(ctypes.byref(a), ctypes.byref(bb), ctypes.byref(base),
+                               cache_path.encode() if cache_path else None, ctypes.byref(best), ctypes.byref(ms)))
+    return {"light_max": best.light_max, "slab_rows": best.slab_rows, "ms": ms.value}
+
+
+def spgemm_batch_destroy(batch: Batch):
+    if batch.handle:
+        _check(_batch_lib().spgemm_batch_destroy(batch.handle))
+        batch.handle = None

@@ -1,0 +1,598 @@
+// Batched execution of many independent products C_i = A_i * B_i in one
+// persistent kernel launch (captured once in a CUDA graph), driven by a device
+// work queue.  An extension beyond the paper: its local multiply (Algorithm 1,
+// last step, Gustavson column by column) run for hundreds of uneven problems at
+// once; each instance is one column block (P = 1), so A_i is read in place
+// (gathering the single block would copy A_i whole).
+//
+// Queue: every instance is cut into tasks of `task_cols` consecutive columns.
+// The queue holds all symbolic tasks, then all numeric tasks; a warp takes one
+// task at a time (a global atomic counter).
+//   symbolic task: per column, a warp hash of row ids gives nnz(C_i(:,j)); the
+//     warp that finishes an instance's last symbolic task scans its counts into
+//     the instance's column pointers and publishes a ready flag;
+//   numeric task: waits (bounded) for the instance's flag, then per column a
+//     warp hash of (row, value), compaction, bitonic sort, and the column is
+//     written at its place.
+// Because all symbolic tasks precede all numeric ones in the queue, a warp
+// that waits only waits for warps that already hold their tasks.  The wait is
+// bounded: after `timeout_ns` it records SPG_TIMEOUT and the kernel returns.
+// Output: one pool for all instances; instance i owns [out_base_i,
+// out_base_i + bound_i) where bound_i = sum_j min(flops_j, m_i) (from the
+// bounds pass at creation), of which it uses its nnz.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "block_ops.cuh"
+#include "spg_internal.cuh"
+
+namespace spg {
+
+const char *last_error_str();
+void clear_error();
+
+struct BatchInst {
+    const void *Acp, *Bcp, *Aval, *Bval;
+    const int32_t *Arow, *Brow;
+    int64_t m, k, n;
+    int64_t out_base;     // first entry of the output region
+    int64_t col_base;     // first column of the instance in the batch-wide column arrays
+    int32_t acp64, bcp64;
+    int32_t ntask;        // column tasks of the instance
+    int32_t vt;           // value type of A and B
+};
+
+struct BatchTask {
+    int32_t inst, c0, c1, pad;
+};
+
+constexpr int kBatchMaxLogS = 11;  // per-warp tables of up to 2048 slots
+enum : int { kBatchErrTimeout = 8 };
+
+template <typename Acc>
+__device__ __forceinline__ Acc bval_load(const void *v, int vt, int64_t i) {
+    if (vt == SPG_VAL_F64) return (Acc)__ldg((const double *)v + i);
+    if (vt == SPG_VAL_I32) return (Acc)__ldg((const int *)v + i);
+    return (Acc)__ldg((const long long *)v + i);
+}
+template <>
+__device__ __forceinline__ double bval_load<double>(const void *v, int, int64_t i) {
+    return __ldg((const double *)v + i);
+}
+template <>
+__device__ __forceinline__ long long bval_load<long long>(const void *v, int vt, int64_t i) {
+    return vt == SPG_VAL_I32 ? (long long)__ldg((const int *)v + i) : __ldg((const long long *)v + i);
+}
+
+// Per column: flops_j and U_j = min(flops_j, m); per instance: sum of U_j
+// (the output bound) and max U_j (the table size).
+__global__ void k_batch_bounds(const BatchInst *insts, const BatchTask *tasks, int64_t ntasks,
+                               unsigned long long *bound, unsigned int *maxU) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp; t < ntasks; t += nw) {
+        const BatchTask tk = tasks[t];
+        const BatchInst in = insts[tk.inst];
+        unsigned long long sum = 0;
+        unsigned int mx = 0;
+        for (int j = tk.c0; j < tk.c1; j++) {
+            const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
+            long long fl = 0;
+            for (int64_t p = p0 + lane; p < p1; p += 32) {
+                const int k = in.Brow[p];
+                fl += ld_ptr(in.Acp, in.acp64, k + 1) - ld_ptr(in.Acp, in.acp64, k);
+            }
+            fl = warp_sum_ll(fl);
+            const long long U = min(fl, (long long)in.m);
+            sum += (unsigned long long)U;
+            mx = max(mx, (unsigned int)min(U, (long long)UINT32_MAX));
+        }
+        if (lane == 0) {
+            atomicAdd(bound + tk.inst, sum);
+            atomicMax(maxU + tk.inst, mx);
+        }
+    }
+}
+
+__device__ __forceinline__ int log_table(long long U) {
+    int l = 6;
+    while ((1ll << l) < 2 * U) l++;
+    return l;
+}
+
+template <typename Acc, typename OutIdx>
+__global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const BatchTask *__restrict__ tasks,
+                                   int64_t ntasks, unsigned long long *head, int *sym_done, int *ready,
+                                   int64_t *nnz, int64_t *colptr, OutIdx *__restrict__ out_row,
+                                   Acc *__restrict__ out_val, int *err, long long timeout_ns, int stall_inst) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int S_MAX = 1 << kBatchMaxLogS;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    WarpSeg<Acc> *segs = (WarpSeg<Acc> *)smem_raw;
+    Acc *vals_all = (Acc *)(segs + nwarps);
+    int *keys_all = (int *)(vals_all + nwarps * S_MAX);
+    int *keys = keys_all + wid * S_MAX;
+    Acc *vals = vals_all + wid * S_MAX;
+    WarpSeg<Acc> &ws = segs[wid];
+    while (true) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(head, 1ull);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= (unsigned long long)(2 * ntasks)) break;
+        const bool numeric = t >= (unsigned long long)ntasks;
+        const BatchTask tk = tasks[numeric ? t - ntasks : t];
+        const BatchInst in = insts[tk.inst];
+        const int64_t colb = in.col_base;
+        auto seg = [&](int64_t p, long long &st, int &len, Acc &bv) {
+            const int k = in.Brow[p];
+            st = ld_ptr(in.Acp, in.acp64, k);
+            len = (int)(ld_ptr(in.Acp, in.acp64, k + 1) - st);
+            bv = bval_load<Acc>(in.Bval, in.vt, p);
+        };
+        if (!numeric) {
+            for (int j = tk.c0; j < tk.c1; j++) {
+                const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
+                // table size from this column's bound min(flops, m)
+                long long fl = 0;
+                for (int64_t p = p0 + lane; p < p1; p += 32) {
+                    const int k = in.Brow[p];
+                    fl += ld_ptr(in.Acp, in.acp64, k + 1) - ld_ptr(in.Acp, in.acp64, k);
+                }
+                fl = warp_sum_ll(fl);
+                const int logS = log_table(min(fl, (long long)in.m));
+                const int S = 1 << logS;
+                for (int s = lane; s < S; s += 32) keys[s] = kEmptyKey;
+                __syncwarp();
+                int cnt = 0;
+                bool full = false;
+                warp_products<false, Acc>(
+                    p0, p1, lane, ws, in.Arow, (const Acc *)nullptr, seg, [&](int r, Acc) {
+                        bool fresh;
+                        if (hash_insert(keys, logS, r, &fresh) < 0) full = true;
+                        cnt += fresh ? 1 : 0;
+                    });
+                cnt = warp_sum_i(cnt);
+                if (__any_sync(kFull, full) && lane == 0) atomicOr(err, kDevErrInternal);
+                if (lane == 0) nnz[colb + j] = cnt;
+                __syncwarp();
+            }
+            int mine = 0;
+            if (lane == 0) {
+                __threadfence();
+                // the warp finishing the instance's last symbolic task scans it
+                mine = atomicAdd(sym_done + tk.inst, 1) + 1 == in.ntask ? 1 : 0;
+            }
+            mine = __shfl_sync(kFull, mine, 0);
+            if (mine) {
+                __threadfence();
+                int64_t run = 0;
+                for (int64_t j0 = 0; j0 < in.n; j0 += 32) {
+                    const int64_t j = j0 + lane;
+                    const int64_t v = j < in.n ? *(volatile int64_t *)(nnz + colb + j) : 0;
+                    int64_t inc = v;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int64_t x = __shfl_up_sync(kFull, inc, o);
+                        if (lane >= o) inc += x;
+                    }
+                    if (j < in.n) colptr[colb + tk.inst + j] = run + inc - v;
+                    run += __shfl_sync(kFull, inc, 31);
+                }
+                if (lane == 0) {
+                    colptr[colb + tk.inst + in.n] = run;
+                    __threadfence();
+                    atomicExch(ready + tk.inst, 1);
+                }
+                __syncwarp();
+            }
+        } else {
+            // wait, bounded, for the instance's column pointers
+            int ok = 0;
+            if (lane == 0) {
+                const int *flag = ready + tk.inst;
+                int never = 0;
+                if (tk.inst == stall_inst) flag = &never;  // failure test: a flag nothing sets
+                unsigned long long start = 0, now = 0;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(start));
+                while (true) {
+                    if (*(volatile const int *)flag == 1) {
+                        ok = 1;
+                        break;
+                    }
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+                    if ((long long)(now - start) > timeout_ns) break;
+                    __nanosleep(256);
+                }
+                if (!ok) atomicOr(err, kBatchErrTimeout);
+                __threadfence();
+            }
+            ok = __shfl_sync(kFull, ok, 0);
+            if (!ok) break;
+            const int64_t *cp = colptr + colb + tk.inst;
+            for (int j = tk.c0; j < tk.c1; j++) {
+                const int64_t base = in.out_base + cp[j];
+                const int64_t want = cp[j + 1] - cp[j];
+                const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
+                const int logS = log_table(want > 0 ? want : 1);
+                const int S = 1 << logS;
+                for (int s = lane; s < S; s += 32) {
+                    keys[s] = kEmptyKey;
+                    vals[s] = Acc(0);
+                }
+                __syncwarp();
+                bool full = false;
+                // A's values may be stored as double, int32 or int64: load them here
+                {
+                    for (int64_t b0 = p0; b0 < p1; b0 += 32) {
+                        const int64_t p = b0 + lane;
+                        long long st = 0;
+                        int len = 0;
+                        Acc bv = Acc(0);
+                        if (p < p1) seg(p, st, len, bv);
+                        int incl = len;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            int x = __shfl_up_sync(kFull, incl, o);
+                            if (lane >= o) incl += x;
+                        }
+                        const int total = __shfl_sync(kFull, incl, 31);
+                        ws.pref[lane] = incl - len;
+                        ws.start[lane] = st;
+                        ws.bv[lane] = bv;
+                        __syncwarp();
+                        for (int f0 = 0; f0 < total; f0 += 32) {
+                            const int fi = f0 + lane;
+                            if (fi < total) {
+                                int s = 0;
+#pragma unroll
+                                for (int stp = 16; stp > 0; stp >>= 1)
+                                    if (ws.pref[s + stp] <= fi) s += stp;
+                                const long long e = ws.start[s] + (fi - ws.pref[s]);
+                                const int r = __ldg(in.Arow + e);
+                                const Acc v = mul_acc<Acc>(bval_load<Acc>(in.Aval, in.vt, e), ws.bv[s]);
+                                bool fresh;
+                                const int slot = hash_insert(keys, logS, r, &fresh);
+                                if (slot < 0)
+                                    full = true;
+                                else
+                                    atomic_add_acc(vals + slot, v);
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                __syncwarp();
+                int nout = 0;
+                for (int c0 = 0; c0 < S; c0 += 32) {
+                    const int kk = keys[c0 + lane];
+                    const Acc vv = vals[c0 + lane];
+                    const bool occ = kk != kEmptyKey;
+                    const unsigned bal = __ballot_sync(kFull, occ);
+                    __syncwarp();
+                    if (occ) {
+                        const int pos = nout + __popc(bal & ((1u << lane) - 1u));
+                        keys[pos] = kk;
+                        vals[pos] = vv;
+                    }
+                    nout += __popc(bal);
+                    __syncwarp();
+                }
+                full = __any_sync(kFull, full);
+                if (full || nout != want) {
+                    if (lane == 0) atomicOr(err, kDevErrInternal);
+                } else {
+                    int npad = 1;
+                    while (npad < nout) npad <<= 1;
+                    for (int s = nout + lane; s < npad; s += 32) keys[s] = INT32_MAX;
+                    __syncwarp();
+                    warp_bitonic<Acc>(keys, vals, npad, lane);
+                    for (int s = lane; s < nout; s += 32) {
+                        out_row[base + s] = (OutIdx)keys[s];
+                        out_val[base + s] = vals[s];
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
+}  // namespace spg
+
+struct spg_batch {
+    int count = 0;
+    int64_t total_cols = 0, ntasks = 0, pool = 0;
+    bool f64 = true;
+    spg_batch_options opt{};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<spg::BatchInst> hinst;
+    std::vector<void *> allocs;
+    spg::BatchInst *insts = nullptr;
+    spg::BatchTask *tasks = nullptr;
+    unsigned long long *head = nullptr;
+    int *sym_done = nullptr, *ready = nullptr, *err = nullptr;
+    int64_t *nnz = nullptr, *colptr = nullptr;
+    void *out_row = nullptr, *out_val = nullptr;
+    int grid = 0, warps = 8;
+    size_t smem = 0;
+    int sm_count = 0;
+};
+
+using namespace spg;
+
+static void *batch_alloc(spg_batch *b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("batch allocation of %zu bytes failed", bytes);
+        return nullptr;
+    }
+    b->allocs.push_back(p);
+    return p;
+}
+
+extern "C" void spgemm_batch_default_options(spg_batch_options *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->task_cols = 64;
+    o->warps_per_cta = 8;
+    o->timeout_ns = 2000000000ll;
+    o->stall_instance = -1;
+}
+
+extern "C" spg_status spgemm_batch_destroy(spg_batch *b) {
+    if (!b) return SPG_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaDeviceSynchronize();
+    for (void *p : b->allocs) cudaFree(p);
+    delete b;
+    return SPG_OK;
+}
+
+template <typename Acc, typename OutIdx>
+static spg_status batch_capture(spg_batch *b) {
+    auto kern = k_batch_persistent<Acc, OutIdx>;
+    spg_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem),
+                              "batch smem");
+    if (s) return s;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, b->warps * 32, b->smem);
+    if (occ < 1) {
+        set_error("batch kernel does not fit on an SM with %d warps", b->warps);
+        return SPG_UNSUPPORTED;
+    }
+    b->grid = b->sm_count * occ;
+    s = cuda_check(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
+    if (s) return s;
+    cudaMemsetAsync(b->head, 0, sizeof(unsigned long long), b->cap_stream);
+    cudaMemsetAsync(b->sym_done, 0, sizeof(int) * (size_t)b->count * 2 + sizeof(int) * 4, b->cap_stream);
+    kern<<<b->grid, b->warps * 32, b->smem, b->cap_stream>>>(
+        b->insts, b->tasks, b->ntasks, b->head, b->sym_done, b->ready, b->nnz, b->colptr, (OutIdx *)b->out_row,
+        (Acc *)b->out_val, b->err, b->opt.timeout_ns, b->opt.stall_instance);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &b->graph);
+    if (le != cudaSuccess) return cuda_check(le, "batch kernel launch");
+    s = cuda_check(e, "end capture");
+    if (s) return s;
+    return cuda_check(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
+}
+
+extern "C" spg_status spgemm_batch_create(int32_t count, const spg_csc *A, const spg_csc *B,
+                                          const spg_batch_options *opt, spg_batch **out) {
+    clear_error();
+    if (!out || count < 1 || !A || !B) {
+        set_error("batch needs count >= 1, A, B and out");
+        return SPG_INVALID_ARGUMENT;
+    }
+    *out = nullptr;
+    spg_batch_options o;
+    spgemm_batch_default_options(&o);
+    if (opt) o = *opt;
+    if (o.task_cols < 1 || (o.warps_per_cta != 4 && o.warps_per_cta != 8) || o.timeout_ns <= 0) {
+        set_error("task_cols >= 1, warps_per_cta 4 or 8, timeout_ns > 0");
+        return SPG_INVALID_ARGUMENT;
+    }
+    const bool f64 = A[0].val_type == SPG_VAL_F64;
+    for (int i = 0; i < count; i++) {
+        const spg_csc &a = A[i], &bb = B[i];
+        if (a.ncols != bb.nrows || a.idx_type != SPG_IDX_I32 || bb.idx_type != SPG_IDX_I32 || a.val_type != bb.val_type ||
+            (a.val_type == SPG_VAL_F64) != f64 || (bb.val_type == SPG_VAL_F64) != f64 || !a.colptr || !bb.colptr ||
+            a.nrows >= INT32_MAX || bb.ncols >= INT32_MAX || a.nrows < 0 || bb.ncols < 0) {
+            set_error("instance %d: dimensions, int32 row ids and one value kind (double or integer) for all", i);
+            return SPG_INVALID_ARGUMENT;
+        }
+    }
+    spg_batch *b = new (std::nothrow) spg_batch();
+    if (!b) return SPG_OUT_OF_MEMORY;
+    b->count = count;
+    b->opt = o;
+    b->f64 = f64;
+    b->warps = o.warps_per_cta;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    spg_status s = cuda_check(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream");
+    // instances and tasks
+    std::vector<BatchTask> htask;
+    b->hinst.resize(count);
+    int64_t col = 0;
+    for (int i = 0; i < count && !s; i++) {
+        BatchInst &in = b->hinst[i];
+        in.Acp = A[i].colptr;
+        in.Bcp = B[i].colptr;
+        in.Aval = A[i].vals;
+        in.Bval = B[i].vals;
+        in.Arow = (const int32_t *)A[i].rowidx;
+        in.Brow = (const int32_t *)B[i].rowidx;
+        in.m = A[i].nrows;
+        in.k = A[i].ncols;
+        in.n = B[i].ncols;
+        in.acp64 = A[i].ptr_type == SPG_IDX_I64;
+        in.bcp64 = B[i].ptr_type == SPG_IDX_I64;
+        in.vt = A[i].val_type;
+        in.col_base = col;
+        int nt = 0;
+        for (int64_t c0 = 0; c0 < in.n; c0 += o.task_cols) {
+            htask.push_back({i, (int32_t)c0, (int32_t)std::min<int64_t>(in.n, c0 + o.task_cols), 0});
+            nt++;
+        }
+        if (nt == 0) htask.push_back({i, 0, 0, 0}), nt = 1;  // empty instance: one empty task
+        in.ntask = nt;
+        col += in.n;
+    }
+    b->total_cols = col;
+    b->ntasks = (int64_t)htask.size();
+    if (!s) {
+        b->insts = (BatchInst *)batch_alloc(b, sizeof(BatchInst) * (size_t)count);
+        b->tasks = (BatchTask *)batch_alloc(b, sizeof(BatchTask) * (size_t)b->ntasks);
+        b->head = (unsigned long long *)batch_alloc(b, sizeof(unsigned long long));
+        b->sym_done = (int *)batch_alloc(b, sizeof(int) * (size_t)count * 2 + sizeof(int) * 4);
+        b->nnz = (int64_t *)batch_alloc(b, sizeof(int64_t) * (size_t)(col + 1));
+        b->colptr = (int64_t *)batch_alloc(b, sizeof(int64_t) * (size_t)(col + count + 1));
+        if (!b->insts || !b->tasks || !b->head || !b->sym_done || !b->nnz || !b->colptr) s = SPG_OUT_OF_MEMORY;
+    }
+    if (!s) {
+        b->ready = b->sym_done + count;
+        b->err = b->ready + count;
+        s = cuda_check(cudaMemcpy(b->insts, b->hinst.data(), sizeof(BatchInst) * (size_t)count, cudaMemcpyHostToDevice), "insts");
+    }
+    if (!s) s = cuda_check(cudaMemcpy(b->tasks, htask.data(), sizeof(BatchTask) * htask.size(), cudaMemcpyHostToDevice), "tasks");
+    // bounds pass: output room and table sizes
+    std::vector<unsigned long long> bound(count);
+    std::vector<unsigned int> maxU(count);
+    if (!s) {
+        unsigned long long *db = (unsigned long long *)batch_alloc(b, sizeof(unsigned long long) * (size_t)count);
+        unsigned int *dm = (unsigned int *)batch_alloc(b, sizeof(unsigned int) * (size_t)count);
+        if (!db || !dm) s = SPG_OUT_OF_MEMORY;
+        if (!s) {
+            cudaMemset(db, 0, sizeof(unsigned long long) * (size_t)count);
+            cudaMemset(dm, 0, sizeof(unsigned int) * (size_t)count);
+            k_batch_bounds<<<grid_for(b->ntasks * 32, 256, b->sm_count * 16), 256>>>(b->insts, b->tasks, b->ntasks, db, dm);
+            s = cuda_check(cudaGetLastError(), "bounds");
+        }
+        if (!s) s = cuda_check(cudaMemcpy(bound.data(), db, sizeof(unsigned long long) * (size_t)count, cudaMemcpyDeviceToHost), "bounds");
+        if (!s) s = cuda_check(cudaMemcpy(maxU.data(), dm, sizeof(unsigned int) * (size_t)count, cudaMemcpyDeviceToHost), "bounds");
+    }
+    if (!s) {
+        unsigned int mx = 0;
+        for (int i = 0; i < count; i++) mx = std::max(mx, maxU[i]);
+        if (mx > (1u << (kBatchMaxLogS - 1))) {
+            set_error("a column of the batch may hold %u entries; the batched path handles <= %d per column "
+                      "(use spgemm_1d_multiply for such products)", mx, 1 << (kBatchMaxLogS - 1));
+            s = SPG_UNSUPPORTED;
+        }
+    }
+    if (!s) {
+        int64_t off = 0;
+        for (int i = 0; i < count; i++) {
+            b->hinst[i].out_base = off;
+            off += (int64_t)bound[i];
+        }
+        b->pool = off;
+        s = cuda_check(cudaMemcpy(b->insts, b->hinst.data(), sizeof(BatchInst) * (size_t)count, cudaMemcpyHostToDevice), "insts");
+        if (!s) {
+            b->out_row = batch_alloc(b, sizeof(int32_t) * (size_t)(off + 1));
+            b->out_val = batch_alloc(b, 8 * (size_t)(off + 1));
+            if (!b->out_row || !b->out_val) s = SPG_OUT_OF_MEMORY;
+        }
+    }
+    if (!s) {
+        const size_t accsz = 8;
+        b->smem = (sizeof(WarpSeg<double>)) * (size_t)b->warps + (accsz + sizeof(int)) * (size_t)b->warps * (1u << kBatchMaxLogS);
+        s = f64 ? batch_capture<double, int>(b) : batch_capture<long long, int>(b);
+    }
+    if (s) {
+        std::string keep = last_error_str();
+        spgemm_batch_destroy(b);
+        set_error("%s", keep.c_str());
+        return s;
+    }
+    *out = b;
+    return SPG_OK;
+}
+
+extern "C" spg_status spgemm_batch_execute(spg_batch *b, void *stream) {
+    clear_error();
+    if (!b) {
+        set_error("batch is NULL");
+        return SPG_INVALID_ARGUMENT;
+    }
+    return cuda_check(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "batch graph launch");
+}
+
+extern "C" spg_status spgemm_batch_status(spg_batch *b, void *stream) {
+    clear_error();
+    if (!b) {
+        set_error("batch is NULL");
+        return SPG_INVALID_ARGUMENT;
+    }
+    int e = 0;
+    spg_status s = cuda_check(cudaMemcpyAsync(&e, b->err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream), "status");
+    if (!s) s = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "status");
+    if (s) return s;
+    if (e & kBatchErrTimeout) {
+        set_error("a batched task waited longer than %lld ns for its instance's column pointers",
+                  (long long)b->opt.timeout_ns);
+        return SPG_TIMEOUT;
+    }
+    if (e) {
+        set_error("batched kernel consistency check failed");
+        return SPG_CUDA_ERROR;
+    }
+    return SPG_OK;
+}
+
+extern "C" spg_status spgemm_batch_result(const spg_batch *b, int32_t i, spg_csc *C) {
+    clear_error();
+    if (!b || !C || i < 0 || i >= b->count) {
+        set_error("bad batch result arguments");
+        return SPG_INVALID_ARGUMENT;
+    }
+    const BatchInst &in = b->hinst[i];
+    int64_t nnz = 0;
+    spg_status s = cuda_check(cudaMemcpy(&nnz, b->colptr + in.col_base + i + in.n, sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost), "result");
+    if (s) return s;
+    C->nrows = in.m;
+    C->ncols = in.n;
+    C->nnz = nnz;
+    C->ptr_type = SPG_IDX_I64;
+    C->idx_type = SPG_IDX_I32;
+    C->val_type = b->f64 ? SPG_VAL_F64 : SPG_VAL_I64;
+    C->colptr = b->colptr + in.col_base + i;
+    C->rowidx = (int32_t *)b->out_row + in.out_base;
+    C->vals = (char *)b->out_val + 8 * in.out_base;
+    return SPG_OK;
+}
+
+extern "C" spg_status spgemm_batch_copy_result(const spg_batch *b, int32_t i, void *colptr, void *rowidx, void *vals,
+                                               void *stream) {
+    spg_csc C{};
+    spg_status s = spgemm_batch_result(b, i, &C);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (colptr)
+        s = cuda_check(cudaMemcpyAsync(colptr, C.colptr, sizeof(int64_t) * (size_t)(C.ncols + 1), cudaMemcpyDeviceToDevice, st), "copy");
+    if (!s && rowidx && C.nnz)
+        s = cuda_check(cudaMemcpyAsync(rowidx, C.rowidx, sizeof(int32_t) * (size_t)C.nnz, cudaMemcpyDeviceToDevice, st), "copy");
+    if (!s && vals && C.nnz)
+        s = cuda_check(cudaMemcpyAsync(vals, C.vals, 8 * (size_t)C.nnz, cudaMemcpyDeviceToDevice, st), "copy");
+    return s;
+}
+
+extern "C" spg_status spgemm_batch_info(const spg_batch *b, int64_t *ntasks, int64_t *pool_entries, int32_t *grid) {
+    if (!b) return SPG_INVALID_ARGUMENT;
+    if (ntasks) *ntasks = b->ntasks;
+    if (pool_entries) *pool_entries = b->pool;
+    if (grid) *grid = b->grid;
+    return SPG_OK;
+}

@@ -1,0 +1,84 @@
+"""Batched persistent execution and the autotuner on the GPU."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2408_14558_gb300 as g
+import synth
+from parity import check_values
+
+pytestmark = pytest.mark.gpu
+
+
+def small_batch(count=24, seed=3, values="f64"):
+    pairs = synth.batch_instances(count, 300, 6000, seed=seed, values=values)
+    As = [g.to_device(A) for A, _ in pairs]
+    Bs = [g.to_device(B) for _, B in pairs]
+    return pairs, As, Bs
+
+
+@pytest.mark.parametrize("values", ["f64", "i64"])
+@pytest.mark.parametrize("task_cols,warps", [(64, 8), (16, 4), (1000, 8)])
+def test_batch_matches_oracle_and_plain(values, task_cols, warps):
+    pairs, As, Bs = small_batch(values=values)
+    batch = g.spgemm_batch_create(As, Bs, task_cols=task_cols, warps_per_cta=warps)
+    for rep in range(2):                      # the graph resets its queue and counters every launch
+        g.spgemm_batch_execute(batch)
+        assert g.spgemm_batch_status(batch) == g.SPG_OK
+        for i in (0, 5, len(pairs) - 1) if rep == 0 else range(len(pairs)):
+            A, B = pairs[i]
+            cp, ri, v = g.spgemm_batch_result(batch, i)
+            ref = oracle.spgemm(A, B)
+            assert np.array_equal(cp.cpu().numpy(), ref["colptr"]), i
+            assert np.array_equal(ri.cpu().numpy().astype(np.int64), ref["rowidx"]), i
+            check_values(v.cpu().numpy(), ref["vals"], ref["absum"], f"instance {i}")
+            if rep == 1 and i < 4:
+                C = g.multiply(As[i], Bs[i], P=1, b=1024)
+                assert torch.equal(C.colptr, cp) and torch.equal(C.rowidx, ri)
+
+
+def test_batch_timeout_is_reported_and_context_survives():
+    """A numeric task waiting on a flag that nothing sets gives up after the
+    timeout; the batch reports SPG_TIMEOUT and the GPU context stays usable."""
+    pairs, As, Bs = small_batch(count=6)
+    bad = g.spgemm_batch_create(As, Bs, timeout_ns=20_000_000, stall_instance=2)
+    g.spgemm_batch_execute(bad)
+    with pytest.raises(g.SpgError) as e:
+        g.spgemm_batch_status(bad)
+    assert e.value.status == g.SPG_TIMEOUT
+    g.spgemm_batch_destroy(bad)
+    good = g.spgemm_batch_create(As, Bs)
+    g.spgemm_batch_execute(good)
+    assert g.spgemm_batch_status(good) == g.SPG_OK
+    cp, ri, v = g.spgemm_batch_result(good, 2)
+    ref = oracle.spgemm(*pairs[2])
+    assert np.array_equal(cp.cpu().numpy(), ref["colptr"])
+
+
+def test_batch_rejects_heavy_columns():
+    A = synth.uniform_columns(3000, 40, seed=1)          # 1600 products per column
+    dA = g.to_device(A)
+    with pytest.raises(g.SpgError) as e:
+        g.spgemm_batch_create([dA], [dA])
+    assert e.value.status == g.SPG_UNSUPPORTED
+
+
+def test_autotuners_write_and_reuse_cache(tmp_path):
+    pairs, As, Bs = small_batch(count=12)
+    path = str(tmp_path / "tune.json")
+    best = g.spgemm_batch_autotune(As, Bs, sample=8, cache_path=path)
+    assert best["task_cols"] in (16, 64, 256) and best["warps_per_cta"] in (4, 8) and best["ms"] > 0
+    again = g.spgemm_batch_autotune(As, Bs, sample=8, cache_path=path)
+    assert (again["task_cols"], again["warps_per_cta"]) == (best["task_cols"], best["warps_per_cta"])
+    A = synth.rmat_symmetric(11, 16, seed=2)
+    dA = g.to_device(A)
+    pb = g.spgemm_autotune(dA, dA, P=4, b=256, cache_path=path)
+    assert pb["light_max"] in (256, 512, 1024) and pb["slab_rows"] in (2048, 4096, 8192)
+    cache = json.load(open(path))
+    assert any("|batch|" in k for k in cache) and any("|plain|" in k for k in cache)
+    C = g.multiply(dA, dA, P=4, b=256, light_max=pb["light_max"], slab_rows=pb["slab_rows"])
+    ref = oracle.spgemm(A, A)
+    assert np.array_equal(C.colptr.cpu().numpy(), ref["colptr"])
