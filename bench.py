@@ -49,6 +49,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rmat18",
+                    choices=["rmat18", "uniform8192", "galerkin128", "similarity", "batched"],
+                    help="rmat18 is the headline; the others measure the remaining configurations")
     return ap.parse_args(argv)
 
 
@@ -247,6 +250,9 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "rmat18":
+        import bench_workloads
+        return bench_workloads.run(args)
     import torch
     import torch.distributed as dist
 

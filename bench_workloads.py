@@ -1,0 +1,214 @@
+"""The configurations other than the headline R-MAT squaring, measured through
+the same C ABI (`python bench.py --workload NAME`); one JSON line each.
+
+    uniform8192  C = A*A, 8192 x 8192, 8 uniform rows per column, f64, P=4, b=256
+    galerkin128  A*P_agg then P_agg^T*(A*P_agg) on the 7-point 128^3 grid, P=32, b=2048
+    similarity   C = A*A^T, A 100,000 x 2^20 lognormal rows / Zipf(1.2) columns, int32
+                 values, int64 result: exact two-pass vs learned sizing (4 column chunks)
+    batched      512 independent ER / R-MAT-row products (n log-uniform in
+                 [1000, 200000], 4..32 per column, f64): one persistent graph
+                 launch vs 512 sequential spgemm_1d_multiply calls
+Every timed region is bracketed by CUDA events on the library's stream, after
+warm-up, with a 256 MiB write that evicts L2 before each timed step.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+FLUSH_BYTES = 256 << 20
+
+
+def _emit(line):
+    print(json.dumps(line), flush=True)
+
+
+def _timer(torch):
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        out = []
+        for s in range(steps):
+            flush.fill_(s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append((e0.elapsed_time(e1), r))
+        return out
+    return timed
+
+
+def _base(workload, metric, value, ms, steps, warmup, dtype, config, **extra):
+    line = {"metric": metric, "value": value, "unit": "GFLOP/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": dict(workload=workload, **config)}
+    line.update(extra)
+    return line
+
+
+def run_uniform(args, torch, g, synth):
+    A = synth.uniform_columns(8192, 8, seed=0)
+    dA = g.to_device(A, ptr_dtype=torch.int32, idx_dtype=torch.int32)
+    timed = _timer(torch)
+
+    def step():
+        plan = g.spgemm_plan(dA, dA, 4, 256)
+        cp, _ = g.spgemm_symbolic(plan)
+        C = g.spgemm_numeric(plan, cp)
+        st = g.spgemm_plan_stats(plan)
+        g.spgemm_plan_destroy(plan)
+        return st
+    res = timed(step, max(args.steps, 20), max(args.warmup, 5))
+    ms = statistics.median(t for t, _ in res)
+    st = res[0][1]
+    _emit(_base("uniform8192_d8_P4_b256", "C=A·A GFLOP/s", 2 * st["products"] / (ms / 1e3) / 1e9, ms, len(res),
+                max(args.warmup, 5), "f64", {"products": st["products"], "nnzC": st["nnzC"]},
+                phase_ms={k: st["ms_" + k] for k in ("plan", "symbolic", "numeric")},
+                gpu_launches=st["kernel_launches"], l2="flushed before every timed step",
+                note="median over steps; the whole multiply is latency bound (tens of kernel launches, host syncs)"))
+
+
+def run_galerkin(args, torch, g, synth):
+    N = 128
+    A, Pg, PT = synth.poisson3d(N), synth.aggregation_2x2x2(N), synth.aggregation_2x2x2_transpose(N)
+    dA, dP, dPT = (g.to_device(M, ptr_dtype=torch.int32, idx_dtype=torch.int32) for M in (A, Pg, PT))
+    timed = _timer(torch)
+
+    def step():
+        plan = g.spgemm_plan(dA, dP, 32, 2048)
+        cp, _ = g.spgemm_symbolic(plan)
+        AP = g.spgemm_numeric(plan, cp)
+        s1 = g.spgemm_plan_stats(plan)
+        g.spgemm_plan_destroy(plan)
+        plan = g.spgemm_plan(dPT, AP, 32, 2048)
+        cp, _ = g.spgemm_symbolic(plan)
+        G = g.spgemm_numeric(plan, cp)
+        s2 = g.spgemm_plan_stats(plan)
+        g.spgemm_plan_destroy(plan)
+        return s1, s2
+    res = timed(step, max(args.steps, 5), max(args.warmup, 3))
+    ms = statistics.median(t for t, _ in res)
+    s1, s2 = res[0][1]
+    prods = s1["products"] + s2["products"]
+    _emit(_base("galerkin_7pt_128cube_P32_b2048", "P^T(A P) GFLOP/s", 2 * prods / (ms / 1e3) / 1e9, ms, len(res),
+                max(args.warmup, 3), "f64",
+                {"products": [s1["products"], s2["products"]], "nnzC": [s1["nnzC"], s2["nnzC"]]},
+                phase_ms=[{k: s["ms_" + k] for k in ("plan", "symbolic", "numeric")} for s in (s1, s2)],
+                gathered_nnz=[s1["gathered_nnz_exact"], s2["gathered_nnz_exact"]],
+                fetch_blocks=[[s["fetch_blocks_chosen"], s["fetch_blocks_total"]] for s in (s1, s2)]))
+
+
+def run_similarity(args, torch, g, synth):
+    from paper_2408_14558_gb300 import learned
+    A, At = synth.lognormal_zipf_rows(seed=0)
+    dA = g.to_device(A, ptr_dtype=torch.int64, idx_dtype=torch.int32)
+    dAt = g.to_device(At, ptr_dtype=torch.int64, idx_dtype=torch.int32)
+    chunks, P = 4, 16
+    n = At.ncols
+    bounds = [(i * n) // chunks for i in range(chunks + 1)]
+    parts = []
+    for c0, c1 in zip(bounds[:-1], bounds[1:]):
+        cp = (dAt.colptr[c0:c1 + 1] - dAt.colptr[c0]).contiguous()
+        s, e = int(dAt.colptr[c0]), int(dAt.colptr[c1])
+        parts.append(g.DeviceCSC(At.nrows, c1 - c0, cp, dAt.rowidx[s:e], dAt.vals[s:e]))
+    if os.path.exists(learned.DEFAULT_MODEL):
+        model = g.spgemm_model_load(learned.DEFAULT_MODEL)
+    else:
+        model = None
+    timed = _timer(torch)
+
+    def run(sizing):
+        stats = []
+        for B in parts:
+            kw = dict(sizing=g.SPG_SIZING_LEARNED, model=model) if sizing else {}
+            C, status = g.spgemm_1d_multiply(dA, B, P=P // chunks, b=1024, **kw)
+            stats.append(g.spgemm_last_multiply_stats())
+            del C
+        return stats
+    ex = timed(lambda: run(False), max(args.steps, 2), max(args.warmup, 1))
+    ms_exact = statistics.median(t for t, _ in ex)
+    prods = sum(s["products"] for s in ex[0][1])
+    nnzc = sum(s["nnzC"] for s in ex[0][1])
+    extra = {"exact_ms": ms_exact, "exact_gflops": 2 * prods / (ms_exact / 1e3) / 1e9}
+    if model is not None:
+        le = timed(lambda: run(True), max(args.steps, 2), max(args.warmup, 1))
+        ms_l = statistics.median(t for t, _ in le)
+        st = le[0][1]
+        rec = sum(s["recomputed_columns"] for s in st)
+        cap = sum(s["learned_capacity"] for s in st)
+        extra.update({"learned_ms": ms_l, "learned_gflops": 2 * prods / (ms_l / 1e3) / 1e9,
+                      "learned_speedup": ms_exact / ms_l, "recomputed_columns": rec,
+                      "recompute_rate": rec / n, "capacity_over_nnz": cap / nnzc})
+        value, ms = extra["learned_gflops"], ms_l
+    else:
+        extra["learned"] = "no model file: run python -m paper_2408_14558_gb300.learned"
+        value, ms = extra["exact_gflops"], ms_exact
+    _emit(_base("similarity_AAt_100k_x_1M_lognormal_zipf", "C=A·Aᵀ GFLOP/s (learned sizing; exact alongside)",
+                value, ms, max(args.steps, 2), max(args.warmup, 1), "int64",
+                {"nnzA": A.nnz, "products": prods, "nnzC": nnzc, "column_chunks": chunks, "P": P, "b": 1024},
+                **extra))
+
+
+def run_batched(args, torch, g, synth):
+    t0 = time.time()
+    pairs = synth.batch_instances(512, 1000, 200000, seed=0)
+    gen_s = time.time() - t0
+    As = [g.to_device(A, ptr_dtype=torch.int32, idx_dtype=torch.int32) for A, _ in pairs]
+    Bs = [g.to_device(B, ptr_dtype=torch.int32, idx_dtype=torch.int32) for _, B in pairs]
+    cache = os.path.join(ROOT, "gpurun_out", "tuning_cache.json")
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    tune = g.spgemm_batch_autotune(As, Bs, sample=64, cache_path=cache)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch = g.spgemm_batch_create(As, Bs, task_cols=tune["task_cols"], warps_per_cta=tune["warps_per_cta"])
+    torch.cuda.synchronize()
+    create_ms = 1e3 * (time.perf_counter() - t0)
+    timed = _timer(torch)
+
+    def run_batch():
+        g.spgemm_batch_execute(batch)
+    res = timed(run_batch, max(args.steps, 3), max(args.warmup, 2))
+    assert g.spgemm_batch_status(batch) == g.SPG_OK
+    ms_b = statistics.median(t for t, _ in res)
+
+    def run_seq():
+        prods = 0
+        for A, B in zip(As, Bs):
+            C, _ = g.spgemm_1d_multiply(A, B, P=1, b=1024)
+            prods += g.spgemm_last_multiply_stats()["products"]
+            del C
+        return prods
+    seq = timed(run_seq, 2, 1)
+    ms_s = statistics.median(t for t, _ in seq)
+    prods = seq[0][1]
+    info = g.spgemm_batch_info(batch)
+    _emit(_base("batched_512_er_rmat_n1e3_2e5_d4_32", "batched C_j=A_j·B_j GFLOP/s (one persistent graph launch)",
+                2 * prods / (ms_b / 1e3) / 1e9, ms_b, len(res), max(args.warmup, 2), "f64",
+                {"instances": 512, "products": prods, "tuned": tune, "tasks": info["tasks"],
+                 "grid": info["grid"], "pool_entries": info["pool_entries"]},
+                sequential_ms=ms_s, sequential_gflops=2 * prods / (ms_s / 1e3) / 1e9, speedup_vs_sequential=ms_s / ms_b,
+                batch_create_ms=create_ms, generation_s=gen_s))
+
+
+def run(args):
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_2408_14558_gb300 as g
+    import synth
+    g.load_library()
+    fn = {"uniform8192": run_uniform, "galerkin128": run_galerkin, "similarity": run_similarity,
+          "batched": run_batched}[args.workload]
+    fn(args, torch, g, synth)
+    return 0

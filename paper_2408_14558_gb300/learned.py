@@ -75,4 +75,18 @@ def train_default_model(path: str | None = None, count: int = 200, epochs: int =
     return model, loss, int(y.numel())
 
 
-__all__ = ["column_data", "training_instances", "training_set", "train_default_model", "SPG_SIZING_LEARNED"]
+__all__ = ["column_data", "training_instances", "training_set", "train_default_model", "SPG_SIZING_LEARNED",
+           "DEFAULT_MODEL"]
+
+import os as _os
+
+DEFAULT_MODEL = _os.path.join(_os.path.dirname(_os.path.abspath(__file__)), "models", "nnz_mlp.bin")
+
+if __name__ == "__main__":
+    import sys
+    import time
+    out = sys.argv[1] if len(sys.argv) > 1 else DEFAULT_MODEL
+    _os.makedirs(_os.path.dirname(out), exist_ok=True)
+    t0 = time.time()
+    model, loss, nsamples = train_default_model(out)
+    print(f"trained on {nsamples} columns of 200 instances in {time.time() - t0:.1f} s, final MSE {loss:.4f} -> {out}")
