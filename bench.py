@@ -25,6 +25,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -49,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--out-dir", default=os.path.join(tempfile.gettempdir(), "spgemm1d_bench"),
+                    help="where the clock samples and the tuning cache are written")
     ap.add_argument("--workload", default="rmat18",
                     choices=["rmat18", "uniform8192", "galerkin128", "similarity", "batched"],
                     help="rmat18 is the headline; the others measure the remaining configurations")
@@ -104,10 +107,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, out_dir: str):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(out_dir, f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
@@ -191,7 +194,7 @@ def run_reference(args):
 
 def _source_digest():
     h = hashlib.sha256()
-    for name in ("numeric.cu", "symbolic.cu", "spg_internal.cuh", "plan.cu"):
+    for name in ("numeric.cu", "symbolic.cu", "spg_internal.cuh", "cta_products.cuh", "block_ops.cuh", "plan.cu"):
         with open(os.path.join(ROOT, "paper_2408_14558_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -212,7 +215,7 @@ def profiled_traffic(kernel: str):
 
 
 def kernel_bytes(group: str, st: dict) -> float:
-    """Algorithmic bytes of one launch group of one run (see DESIGN.md):
+    """Algorithmic bytes of one launch group of one run:
     numeric heavy: write its C entries, read its B entries and A~ once;
     numeric light: the same for the light columns; symbolic: read B rows and
     A~ rows once, write one count per column; gather: read and write A~."""
@@ -284,7 +287,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.out_dir)
     clocks.start()
     times, stats = [], []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

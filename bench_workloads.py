@@ -167,7 +167,7 @@ def run_batched(args, torch, g, synth):
     gen_s = time.time() - t0
     As = [g.to_device(A, ptr_dtype=torch.int32, idx_dtype=torch.int32) for A, _ in pairs]
     Bs = [g.to_device(B, ptr_dtype=torch.int32, idx_dtype=torch.int32) for _, B in pairs]
-    cache = os.path.join(ROOT, "gpurun_out", "tuning_cache.json")
+    cache = os.path.join(args.out_dir, "tuning_cache.json")
     os.makedirs(os.path.dirname(cache), exist_ok=True)
     tune = g.spgemm_batch_autotune(As, Bs, sample=64, cache_path=cache)
     torch.cuda.synchronize()

@@ -108,36 +108,34 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
                 int s = 0;
                 for (int stp = kBatch >> 1; stp > 0; stp >>= 1)
                     if (s + stp < nl && sb.pref[s + stp] <= c0) s += stp;
-                for (int c = c0; c < c1; c += U) {
-                    int su[U];
-                    bool ok[U];
-                    long long e[U];
+                // segment by segment: the chunks of segment s inside [c0, c1)
+                for (int c = c0; c < c1; s++) {
+                    const int sp = sb.pref[s];
+                    const int cend = min(c1, s + 1 < nl ? sb.pref[s + 1] : nch);
+                    const int skip = (c - sp) << 5;
+                    const long long st = sb.start[s] + skip + lane;
+                    const int rem = sb.len[s] - skip - lane;  // entries left for this lane's first chunk
+                    const Acc bvs = NEED_VAL ? sb.bv[s] : Acc(0);
+                    const int nck = cend - c;
+                    for (int k = 0; k < nck; k += U) {
+                        int r[U];
+                        Acc a[U];
+                        bool ok[U];
 #pragma unroll
-                    for (int u = 0; u < U; u++) {
-                        const int cu = c + u;
-                        int x = u == 0 ? s : su[u - 1];
-                        if (cu < c1)
-                            while (x + 1 < nl && sb.pref[x + 1] <= cu) x++;
-                        su[u] = x;
-                        const int o = ((cu - sb.pref[x]) << 5) + lane;
-                        ok[u] = cu < c1 && o < sb.len[x];
-                        e[u] = sb.start[x] + o;
-                    }
-                    int r[U];
-                    Acc a[U];
-#pragma unroll
-                    for (int u = 0; u < U; u++) {
-                        r[u] = 0;
-                        a[u] = Acc(0);
-                        if (ok[u]) {
-                            r[u] = __ldg(At_row + e[u]);
-                            if (NEED_VAL) a[u] = __ldg(At_val + e[u]);
+                        for (int u = 0; u < U; u++) {
+                            ok[u] = k + u < nck && ((k + u) << 5) < rem;
+                            r[u] = 0;
+                            a[u] = Acc(0);
+                            if (ok[u]) {
+                                r[u] = __ldg(At_row + st + ((k + u) << 5));
+                                if (NEED_VAL) a[u] = __ldg(At_val + st + ((k + u) << 5));
+                            }
                         }
-                    }
 #pragma unroll
-                    for (int u = 0; u < U; u++)
-                        if (ok[u]) body(r[u], NEED_VAL ? mul_acc<Acc>(a[u], sb.bv[su[u]]) : Acc(0));
-                    s = su[U - 1];
+                        for (int u = 0; u < U; u++)
+                            if (ok[u]) body(r[u], NEED_VAL ? mul_acc<Acc>(a[u], bvs) : Acc(0));
+                    }
+                    c = cend;
                 }
             }
         }

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 // The accumulator is cleared row by row as it is read, so it is zero again
 // for the next item.
 template <typename Acc, typename OutIdx>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kBatch)
     k_fused_heavy(int64_t nitems, const int32_t *__restrict__ it_rec0, const int32_t *__restrict__ it_nrec,
                   const int32_t *__restrict__ rec_col, const int32_t *__restrict__ rec_slab, const void *Bcolptr,
                   int p64, const int32_t *__restrict__ Bq, const Acc *__restrict__ Bv,
@@ -818,9 +818,9 @@ static spg_status learned_kernels(spg_plan *p, LearnedState &L) {
     auto kern = k_fused_heavy<Acc, OutIdx>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBatch, smem);
     if (occ < 1) occ = 1;
-    launch(p, kern, grid_for(L.nitems, 1, p->sm_count * occ), 256, smem, L.nitems, L.it_rec0, L.it_nrec, p->rec_col,
+    launch(p, kern, grid_for(L.nitems, 1, p->sm_count * occ), kBatch, smem, L.nitems, L.it_rec0, L.it_nrec, p->rec_col,
            p->rec_slab, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv, p->At_colptr, p->At_row,
            (const Acc *)p->At_val, p->split, p->T, p->R, L.capoff, L.cap, L.colfill, L.flag, L.nflag, L.item_cnt,
            L.item_pos, (OutIdx *)L.trow, (Acc *)L.tval);

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 // the lower bits); products accumulate at acc[rank]; the item is then written
 // at its final place in C, values as one coalesced run and rows word by word.
 template <typename Acc, typename OutIdx>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kBatch)
     k_num_heavy(int64_t nitems, const int32_t *__restrict__ num_rec0, const int32_t *__restrict__ num_nrec,
                 const int32_t *__restrict__ rec_col, const int32_t *__restrict__ rec_slab,
                 const int32_t *__restrict__ rec_cnt, const int64_t *__restrict__ rec_off,
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256)
     const int RW = R >> 5;
     CtaBatch<Acc> &sb = *(CtaBatch<Acc> *)smem_raw;
     Acc *acc = (Acc *)(smem_raw + ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15));
-    uint2 *bp = (uint2 *)(acc + cap);  // (bitmap word, exclusive prefix of popcounts)
+    uint2 *bp = (uint2 *)(acc + cap + 1);  // (bitmap word, exclusive prefix of popcounts)
     __shared__ int wsum[33];
     __shared__ int bad_sh;
     if (threadIdx.x == 0) bad_sh = 0;
@@ -147,11 +147,13 @@ __global__ void __launch_bounds__(256)
                 }
             },
             [&](int r, Acc v) {
+                // a row missing from the symbolic bitmap (never expected) goes to
+                // the dump slot acc[cap] and is reported
                 const uint2 x = bp[(r >> 5) - wbase];
-                if (!((x.x >> (r & 31)) & 1u))
-                    miss = true;
-                else
-                    atomic_add_acc(acc + x.y + __popc(x.x & ((1u << (r & 31)) - 1u)), v);
+                const uint32_t sh = r & 31;
+                const bool hit = (x.x >> sh) & 1u;
+                miss |= !hit;
+                atomic_add_acc(acc + (hit ? (int)(x.y + __popc(x.x & ((1u << sh) - 1u))) : cap), v);
             });
         if (miss) bad_sh = 1;
         // cta_products ends with a barrier: acc is complete
@@ -228,8 +230,8 @@ static spg_status numeric_typed(spg_plan *p, spg_csc *C) {
     if (any_light) group_end(p, kKNumLight);
     if (s) return s;
     if (p->nnum > 0) {
-        const int threads = 256;
-        size_t smem = ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15) + sizeof(Acc) * (size_t)p->num_cap +
+        const int threads = kBatch;
+        size_t smem = ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15) + sizeof(Acc) * (size_t)(p->num_cap + 1) +
                       sizeof(uint2) * (size_t)kNumMaxWords;
         auto kern = k_num_heavy<Acc, OutIdx>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

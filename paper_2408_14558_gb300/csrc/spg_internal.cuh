@@ -265,7 +265,11 @@ constexpr int kNumMaxWords = 4096;
 #ifndef SPG_SYM_UNROLL
 #define SPG_SYM_UNROLL 8
 #endif
-constexpr int kBatch = 256;   // B' entries staged per round by cta_products
+#ifndef SPG_HEAVY_THREADS
+#define SPG_HEAVY_THREADS 256
+#endif
+// threads of a heavy-bin CTA = B' entries staged per round by cta_products
+constexpr int kBatch = SPG_HEAVY_THREADS;
 constexpr int kLongSeg = 32;  // segments this long are walked 32 entries per warp step
 
 __device__ __forceinline__ unsigned hash_row(int r, int shift) {

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 // One CTA per symbolic item: records [r0, r0 + nr) of one heavy column, i.e.
 // base slabs t0 .. t0 + nr - 1.  Every product sets its row's bit; then the
 // bitmap of each record and its population count are stored.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kBatch)
     k_sym_heavy(int64_t nitems, const int32_t *__restrict__ sym_rec0, const int32_t *__restrict__ sym_nrec,
                 const int32_t *__restrict__ rec_col, const int32_t *__restrict__ rec_slab, const void *Bcolptr,
                 int p64, const int32_t *__restrict__ Bq, const int64_t *__restrict__ At_colptr,
@@ -170,7 +170,7 @@ static spg_status launch_sym_light(spg_plan *p, const int32_t *list, int64_t cnt
 
 static spg_status symbolic_heavy(spg_plan *p) {
     cudaStream_t st = p->st;
-    const int threads = 256;
+    const int threads = kBatch;
     size_t smem = sizeof(CtaBatch<long long>) + sizeof(uint32_t) * (size_t)kSymMaxWords;
     cudaFuncSetAttribute(k_sym_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
