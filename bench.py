@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "C=A·B GFLOP/s & % HBM roofline; learned/batched vs plain GPU time, exact C"
-WORKLOAD = "rmat_s18_ef16_symmetric_squaring"
+RMAT_SCALE = 18                # the headline workload: R-MAT scale 18, edge factor 16
 P_BLOCKS, FETCH_B = 16, 1024
 CPU_SAMPLE_COLS = 65536      # columns of C computed by the oracle for the CPU baseline
 REF_SAMPLE_COLS = 16384      # per step of the reference arm
@@ -55,6 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="rmat18",
                     choices=["rmat18", "uniform8192", "galerkin128", "similarity", "batched"],
                     help="rmat18 is the headline; the others measure the remaining configurations")
+    ap.add_argument("--rmat-scale", type=int, default=RMAT_SCALE,
+                    help="R-MAT scale of the rmat18 workload (smaller scales for profiler captures)")
     return ap.parse_args(argv)
 
 
@@ -69,17 +71,21 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def make_workload():
+def workload_name(scale: int) -> str:
+    return f"rmat_s{scale}_ef16_symmetric_squaring"
+
+
+def make_workload(scale: int):
     import synth
-    A = synth.rmat_symmetric(18, 16, seed=0)
+    A = synth.rmat_symmetric(scale, 16, seed=0)
     Ai = synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx, A.vals.astype(np.int64))
     return A, Ai
 
 
-def workload_config(products_per_run, nnzC):
-    return {"workload": WORKLOAD, "P": P_BLOCKS, "b": FETCH_B,
+def workload_config(scale, products_per_run, nnzC):
+    return {"workload": workload_name(scale), "P": P_BLOCKS, "b": FETCH_B,
             "runs_per_step": ["f64 values 1.0", "int64 path counts"],
-            "n": 1 << 18, "nnzA": None, "products_per_run": products_per_run, "nnzC_per_run": nnzC,
+            "n": 1 << scale, "nnzA": None, "products_per_run": products_per_run, "nnzC_per_run": nnzC,
             "index_types": "int32 colptr / int32 row ids", "l2": "flushed before every timed step (256 MiB write)"}
 
 
@@ -169,7 +175,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    A, _ = make_workload()
+    A, _ = make_workload(args.rmat_scale)
     for w in range(args.warmup):
         time_oracle(A, REF_SAMPLE_COLS, seed=100 + w)
     secs, prods = [], []
@@ -182,7 +188,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(None, None),
+            "config": workload_config(args.rmat_scale, None, None),
             "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": f"each step: {REF_SAMPLE_COLS} random output columns of the f64 run"},
             "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -200,10 +206,10 @@ def _source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str):
+def profiled_traffic(kernel: str, scale: int):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
     if there is none or the sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_rmat_s18.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_rmat_s{scale}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -265,7 +271,7 @@ def main(argv=None):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     g.load_library()
-    A, Ai = make_workload()
+    A, Ai = make_workload(args.rmat_scale)
     dA = g.to_device(A, ptr_dtype=torch.int32, idx_dtype=torch.int32)
     dAi = g.to_device(Ai, ptr_dtype=torch.int32, idx_dtype=torch.int32)
     stream = torch.cuda.current_stream()
@@ -327,9 +333,9 @@ def main(argv=None):
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+int64", "data": "synthetic",
-            "config": workload_config(stats[0][0]["products"], stats[0][0]["nnzC"]),
+            "config": workload_config(args.rmat_scale, stats[0][0]["products"], stats[0][0]["nnzC"]),
             "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(kernel_name),
+                         "frac": achieved / peak, "traffic": profiled_traffic(kernel_name, args.rmat_scale),
                          "algorithmic_bytes_per_step": dom_bytes, "ms_per_step": dom_ms,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
             "path_roofline": {"compulsory_bytes_per_step": comp, "achieved": path_gbs, "frac": path_gbs / peak,

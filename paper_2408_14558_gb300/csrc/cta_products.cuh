@@ -147,24 +147,37 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
             const long long *sstart = sb.start + nl;
             const Acc *sbv = sb.bv + nl;
             if (f0 < f1) {
+                // s0: the segment holding product f (found once by binary search)
                 int s0 = 0;
                 for (int stp = kBatch >> 1; stp > 0; stp >>= 1)
                     if (s0 + stp < ns && spref[s0 + stp] <= f0) s0 += stp;
                 for (int f = f0; f < f1; f += 32) {
+                    // lane k holds segment s0 + k; segments are non-empty, so the
+                    // window [f, f+32) meets at most s0 .. s0+31, and segment
+                    // s0+k (k >= 1) starts at window position spref - f >= 1
+                    const int sk = s0 + lane;
+                    const int pk = sk < ns ? spref[sk] : 0x7fffffff;
+                    const long long stk = sk < ns ? sstart[sk] : 0;
+                    const Acc bvk = (NEED_VAL && sk < ns) ? sbv[sk] : Acc(0);
+                    const int pos = pk - f;
+                    const uint32_t M = __reduce_or_sync(kFull, (lane > 0 && pos < 32) ? (1u << pos) : 0u);
+                    const int k = __popc(M & ((2u << lane) - 1u));  // segment starts at positions <= lane
+                    const long long st = __shfl_sync(kFull, stk, k);
+                    const int sp = __shfl_sync(kFull, pk, k);
                     const int fi = f + lane;
-                    int lo = s0;
-#pragma unroll
-                    for (int stp = 32; stp > 0; stp >>= 1)
-                        if (lo + stp < ns && spref[lo + stp] <= fi) lo += stp;
-                    if (fi < f1) {
-                        const long long e = sstart[lo] + (fi - spref[lo]);
-                        const int r = __ldg(At_row + e);
-                        if (NEED_VAL)
-                            body(r, mul_acc<Acc>(__ldg(At_val + e), sbv[lo]));
-                        else
-                            body(r, Acc(0));
+                    if (NEED_VAL) {
+                        const Acc b = __shfl_sync(kFull, bvk, k);
+                        if (fi < f1) {
+                            const long long e = st + (fi - sp);
+                            body(__ldg(At_row + e), mul_acc<Acc>(__ldg(At_val + e), b));
+                        }
+                    } else if (fi < f1) {
+                        body(__ldg(At_row + st + (fi - sp)), Acc(0));
                     }
-                    s0 = __shfl_sync(kFull, lo, 31);
+                    // the segment holding product f + 32
+                    int c = __popc(M);
+                    if (s0 + c + 1 < ns && spref[s0 + c + 1] == f + 32) c++;
+                    s0 += c;
                 }
             }
         }

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kBatch)
                 const Acc *__restrict__ Bv, const int64_t *__restrict__ At_colptr,
                 const int32_t *__restrict__ At_row, const Acc *__restrict__ At_val,
                 const int32_t *__restrict__ split, int T, int R, int cap, const int64_t *__restrict__ Ccolptr,
-                OutIdx *__restrict__ Crow, Acc *__restrict__ Cval, int *err) {
+                OutIdx *__restrict__ Crow, Acc *__restrict__ Cval, int *err, unsigned long long *next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RW = R >> 5;
     CtaBatch<Acc> &sb = *(CtaBatch<Acc> *)smem_raw;
@@ -112,8 +112,9 @@ __global__ void __launch_bounds__(kBatch)
     uint2 *bp = (uint2 *)(acc + cap + 1);  // (bitmap word, exclusive prefix of popcounts)
     __shared__ int wsum[33];
     __shared__ int bad_sh;
+    __shared__ long long claim;
     if (threadIdx.x == 0) bad_sh = 0;
-    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    for (int64_t it = cta_claim(next, &claim); it < nitems; it = cta_claim(next, &claim)) {
         const int r0 = num_rec0[it], nr = num_nrec[it];
         const int j = rec_col[r0], t0 = rec_slab[r0];
         const int nwords = nr * RW;
@@ -239,11 +240,13 @@ static spg_status numeric_typed(spg_plan *p, spg_csc *C) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
         if (occ < 1) occ = 1;
         int g = grid_for(p->nnum, 1, p->sm_count * occ);
+        s = cuda_check(cudaMemsetAsync(p->d_cnt + kCntNumNextSlot, 0, sizeof(int64_t), p->st), "memset");
+        if (s) return s;
         group_begin(p, kKNumHeavy);
         launch(p, kern, g, threads, smem, p->nnum, p->num_rec0, p->num_nrec, p->rec_col, p->rec_slab, p->rec_cnt,
                p->rec_off, p->hbits, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv,
                p->At_colptr, p->At_row, (const Acc *)p->At_val, p->split, p->T, p->R, p->num_cap, p->Ccolptr,
-               (OutIdx *)C->rowidx, (Acc *)C->vals, p->d_err);
+               (OutIdx *)C->rowidx, (Acc *)C->vals, p->d_err, (unsigned long long *)(p->d_cnt + kCntNumNextSlot));
         group_end(p, kKNumHeavy);
         s = cuda_check(cudaGetLastError(), "numeric heavy");
     }

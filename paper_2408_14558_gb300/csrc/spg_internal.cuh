@@ -140,6 +140,18 @@ inline void launch(spg_plan *p, void (*kern)(KArgs...), dim3 grid, dim3 block, s
 // Slot of plan->d_cnt that collects nnz(C) of the heavy columns (the other
 // slots are used by the planning kernels).
 constexpr int kCntNnzCHeavySlot = 18;
+// Slots of plan->d_cnt holding the next unclaimed heavy item of the symbolic
+// and numeric heavy kernels (CTAs claim items one at a time, in column order).
+constexpr int kCntSymNextSlot = 19;
+constexpr int kCntNumNextSlot = 20;
+
+// Claim the next item for the whole CTA; every thread must call it, and the
+// CTA must have passed a barrier since the previous claim was read.
+__device__ __forceinline__ int64_t cta_claim(unsigned long long *next, long long *slot) {
+    if (threadIdx.x == 0) *slot = (long long)atomicAdd(next, 1ull);
+    __syncthreads();
+    return *slot;
+}
 
 // Kernel groups timed with their own event pair.
 enum KernelGroup { kKGather = 0, kKSymLight = 1, kKSymHeavy = 2, kKNumLight = 3, kKNumHeavy = 4 };

@@ -58,13 +58,14 @@ __global__ void __launch_bounds__(kBatch)
                 const int32_t *__restrict__ rec_col, const int32_t *__restrict__ rec_slab, const void *Bcolptr,
                 int p64, const int32_t *__restrict__ Bq, const int64_t *__restrict__ At_colptr,
                 const int32_t *__restrict__ At_row, const int32_t *__restrict__ split, int T, int R,
-                uint32_t *__restrict__ hbits, int32_t *__restrict__ rec_cnt) {
+                uint32_t *__restrict__ hbits, int32_t *__restrict__ rec_cnt, unsigned long long *next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RW = R >> 5;
     CtaBatch<long long> &sb = *(CtaBatch<long long> *)smem_raw;
     uint32_t *bits = (uint32_t *)(smem_raw + sizeof(CtaBatch<long long>));
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    __shared__ long long claim;
+    for (int64_t it = cta_claim(next, &claim); it < nitems; it = cta_claim(next, &claim)) {
         const int r0 = sym_rec0[it], nr = sym_nrec[it];
         const int j = rec_col[r0], t0 = rec_slab[r0];
         const int nwords = nr * RW;
@@ -177,10 +178,12 @@ static spg_status symbolic_heavy(spg_plan *p) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sym_heavy, threads, smem);
     if (occ < 1) occ = 1;
     int g = grid_for(p->nsym, 1, p->sm_count * occ);
+    spg_status s0 = cuda_check(cudaMemsetAsync(p->d_cnt + kCntSymNextSlot, 0, sizeof(int64_t), st), "memset");
+    if (s0) return s0;
     group_begin(p, kKSymHeavy);
     launch(p, k_sym_heavy, g, threads, smem, p->nsym, p->sym_rec0, p->sym_nrec, p->rec_col, p->rec_slab,
            p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr, p->At_row, p->split, p->T, p->R,
-           p->hbits, p->rec_cnt);
+           p->hbits, p->rec_cnt, (unsigned long long *)(p->d_cnt + kCntSymNextSlot));
     group_end(p, kKSymHeavy);
     int64_t *nnum = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
     int64_t *num_first = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
