@@ -60,28 +60,46 @@ __device__ __forceinline__ void cta_scan4(const int v[4], int ex[4], int (*wsum)
     for (int q = 0; q < 4; q++) ex[q] = wsum[q][wid] + in[q] - v[q];
 }
 
+// One thread's B' entry of a batch: its A~ segment and its value.
+template <typename Acc>
+struct SegReg {
+    long long st = 0;
+    int len = 0;
+    Acc bv = Acc(0);
+};
+
+// The segment of this thread's entry in the first batch of [p0, p1); callers
+// fetch it early so that its loads overlap their own set-up.
+template <typename Acc, typename SegFn>
+__device__ __forceinline__ SegReg<Acc> cta_first_seg(int64_t p0, int64_t p1, SegFn seg) {
+    SegReg<Acc> r;
+    if (p0 + threadIdx.x < p1) seg(p0 + threadIdx.x, r.st, r.len, r.bv);
+    return r;
+}
+
 // Walk every product of the B' entries [p0, p1) of one output column with the
-// whole CTA (all threads must call it; blockDim.x == kBatch).
+// whole CTA (all threads must call it; blockDim.x == kBatch); `first` is
+// cta_first_seg(p0, p1, seg).
 // seg(p, start, len, bv) gives the A~ positions [start, start+len) that B'
 // entry p multiplies and its value; body(row, product) runs once per product.
-// The chunks of the long segments are shared evenly by the warps (lanes read
-// consecutive entries: no search, coalesced); U chunks are in flight per warp
-// step so that U loads per lane overlap.  The products of short segments are
-// shared evenly too, each lane locating its segment by a binary search over
-// a window of at most 64 segments.  One batch must hold < 2^31 products
-// (heavy items bound their segments to the item's row range).  Ends with a
-// barrier.
+// The segments of the next batch are fetched before the current batch is
+// walked.  The chunks of the long segments are shared evenly by the warps
+// (lanes read consecutive entries, coalesced); each warp step takes the next U
+// chunks of the warp's range, across segment boundaries, so that U loads per
+// lane are in flight however short the segments.  The products of short
+// segments are shared evenly too (a warp bitmask locates each lane's
+// segment).  One batch must hold < 2^31 products (heavy items bound their
+// segments to the item's row range).  Ends with a barrier.
 template <bool NEED_VAL, int U, typename Acc, typename SegFn, typename Body>
 __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Acc> &sb,
                                              const int32_t *__restrict__ At_row, const Acc *__restrict__ At_val,
-                                             SegFn seg, Body body) {
+                                             SegReg<Acc> first, SegFn seg, Body body) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    SegReg<Acc> cur = first;
     for (int64_t b0 = p0; b0 < p1; b0 += kBatch) {
-        const int nb = (int)min((int64_t)kBatch, p1 - b0);
-        long long st = 0;
-        int len = 0;
-        Acc bv = Acc(0);
-        if (tid < nb) seg(b0 + tid, st, len, bv);
+        const long long st = cur.st;
+        const int len = cur.len;
+        const Acc bv = cur.bv;
         const bool is_long = len >= kLongSeg;
         const int v[4] = {is_long ? 1 : 0, is_long ? (len + 31) >> 5 : 0, (!is_long && len > 0) ? 1 : 0,
                           is_long ? 0 : len};
@@ -99,6 +117,7 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
             if (NEED_VAL) sb.bv[nl + ex[2]] = bv;
         }
         __syncthreads();
+        if (b0 + kBatch < p1) cur = cta_first_seg<Acc>(b0 + kBatch, p1, seg);
 
         // long segments: chunks [c0, c1) of this warp, U per step
         {
@@ -108,34 +127,47 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
                 int s = 0;
                 for (int stp = kBatch >> 1; stp > 0; stp >>= 1)
                     if (s + stp < nl && sb.pref[s + stp] <= c0) s += stp;
-                // segment by segment: the chunks of segment s inside [c0, c1)
-                for (int c = c0; c < c1; s++) {
-                    const int sp = sb.pref[s];
-                    const int cend = min(c1, s + 1 < nl ? sb.pref[s + 1] : nch);
-                    const int skip = (c - sp) << 5;
-                    const long long st = sb.start[s] + skip + lane;
-                    const int rem = sb.len[s] - skip - lane;  // entries left for this lane's first chunk
-                    const Acc bvs = NEED_VAL ? sb.bv[s] : Acc(0);
-                    const int nck = cend - c;
-                    for (int k = 0; k < nck; k += U) {
-                        int r[U];
-                        Acc a[U];
-                        bool ok[U];
+                // segment s (chunks [sp, snext)) in registers; chunks are
+                // contiguous and every long segment has one or more, so the
+                // next chunk lies in s or s + 1
+                int sp = sb.pref[s], slen = sb.len[s];
+                int snext = s + 1 < nl ? sb.pref[s + 1] : nch;
+                long long sst = sb.start[s];
+                Acc sbv = NEED_VAL ? sb.bv[s] : Acc(0);
+                for (int c = c0; c < c1; c += U) {
+                    int r[U];
+                    Acc a[U], bu[U];
+                    bool ok[U];
 #pragma unroll
-                        for (int u = 0; u < U; u++) {
-                            ok[u] = k + u < nck && ((k + u) << 5) < rem;
-                            r[u] = 0;
-                            a[u] = Acc(0);
-                            if (ok[u]) {
-                                r[u] = __ldg(At_row + st + ((k + u) << 5));
-                                if (NEED_VAL) a[u] = __ldg(At_val + st + ((k + u) << 5));
+                    for (int u = 0; u < U; u++) {
+                        const int cu = c + u;
+                        ok[u] = false;
+                        r[u] = 0;
+                        a[u] = Acc(0);
+                        bu[u] = Acc(0);
+                        if (cu < c1) {
+                            if (cu == snext) {
+                                s++;
+                                sp = snext;
+                                slen = sb.len[s];
+                                sst = sb.start[s];
+                                if (NEED_VAL) sbv = sb.bv[s];
+                                snext = s + 1 < nl ? sb.pref[s + 1] : nch;
+                            }
+                            const int off = ((cu - sp) << 5) + lane;
+                            if (off < slen) {
+                                ok[u] = true;
+                                r[u] = __ldg(At_row + sst + off);
+                                if (NEED_VAL) {
+                                    a[u] = __ldg(At_val + sst + off);
+                                    bu[u] = sbv;
+                                }
                             }
                         }
-#pragma unroll
-                        for (int u = 0; u < U; u++)
-                            if (ok[u]) body(r[u], NEED_VAL ? mul_acc<Acc>(a[u], bvs) : Acc(0));
                     }
-                    c = cend;
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (ok[u]) body(r[u], NEED_VAL ? mul_acc<Acc>(a[u], bu[u]) : Acc(0));
                 }
             }
         }

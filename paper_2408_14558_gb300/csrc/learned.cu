@@ -333,21 +333,22 @@ __global__ void __launch_bounds__(kBatch)
         const int j = rec_col[r0], t0 = rec_slab[r0];
         const int nwords = nr * RW;
         const long long rbase = (long long)t0 * R;
+        const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
+        auto seg = [&](int64_t p, long long &st, int &len, Acc &bv) {
+            int q = Bq[p];
+            if (q >= 0) {
+                const int32_t *sp = split + (int64_t)q * (T + 1);
+                int a = sp[t0], b = sp[t0 + nr];
+                st = At_colptr[q] + a;
+                len = b - a;
+                bv = Bv[p];
+            }
+        };
+        const SegReg<Acc> first = cta_first_seg<Acc>(p0, p1, seg);
         for (int w = threadIdx.x; w < nwords; w += blockDim.x) bits[w] = 0;
         __syncthreads();
-        const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
         cta_products<true, SPG_NUM_UNROLL, Acc>(
-            p0, p1, sb, At_row, At_val,
-            [&](int64_t p, long long &st, int &len, Acc &bv) {
-                int q = Bq[p];
-                if (q >= 0) {
-                    const int32_t *sp = split + (int64_t)q * (T + 1);
-                    int a = sp[t0], b = sp[t0 + nr];
-                    st = At_colptr[q] + a;
-                    len = b - a;
-                    bv = Bv[p];
-                }
-            },
+            p0, p1, sb, At_row, At_val, first, seg,
             [&](int r, Acc v) {
                 const int lr = (int)(r - rbase);
                 atomicOr(bits + (lr >> 5), 1u << (lr & 31));

@@ -90,21 +90,49 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
+// Everything a numeric item needs before its first product, in one record.
+struct NumItem {
+    int32_t j, t0, nr, cnt, r0, pad;
+    long long cbase, p0, p1;  // first entry of the item in C; B(:, j) = [p0, p1)
+};
+
+__global__ void k_num_headers(int64_t nitems, const int32_t *__restrict__ num_rec0,
+                              const int32_t *__restrict__ num_nrec, const int32_t *__restrict__ rec_col,
+                              const int32_t *__restrict__ rec_slab, const int32_t *__restrict__ rec_cnt,
+                              const int64_t *__restrict__ rec_off, const void *Bcolptr, int p64,
+                              const int64_t *__restrict__ Ccolptr, NumItem *__restrict__ items) {
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        NumItem h;
+        h.r0 = num_rec0[it];
+        h.nr = num_nrec[it];
+        h.j = rec_col[h.r0];
+        h.t0 = rec_slab[h.r0];
+        int cnt = 0;
+        for (int rr = 0; rr < h.nr; rr++) cnt += rec_cnt[h.r0 + rr];
+        h.cnt = cnt;
+        h.pad = 0;
+        h.cbase = Ccolptr[h.j] + rec_off[h.r0];
+        h.p0 = ld_ptr(Bcolptr, p64, h.j);
+        h.p1 = ld_ptr(Bcolptr, p64, h.j + 1);
+        items[it] = h;
+    }
+}
+
 // One CTA per numeric item: records [r0, r0 + nr) of one heavy column (base
 // slabs t0 .. t0 + nr - 1) holding cnt <= cap entries of C.  The symbolic
 // bitmaps of the records give every present row its rank (pre[word] + popc of
 // the lower bits); products accumulate at acc[rank]; the item is then written
-// at its final place in C, values as one coalesced run and rows word by word.
+// at its final place in C, values and rows each as one coalesced run.  Thread
+// 0 claims the next item when the current one starts and fetches its header
+// while the current one is written out.
 template <typename Acc, typename OutIdx>
-__global__ void __launch_bounds__(kBatch)
-    k_num_heavy(int64_t nitems, const int32_t *__restrict__ num_rec0, const int32_t *__restrict__ num_nrec,
-                const int32_t *__restrict__ rec_col, const int32_t *__restrict__ rec_slab,
-                const int32_t *__restrict__ rec_cnt, const int64_t *__restrict__ rec_off,
-                const uint32_t *__restrict__ hbits, const void *Bcolptr, int p64, const int32_t *__restrict__ Bq,
-                const Acc *__restrict__ Bv, const int64_t *__restrict__ At_colptr,
+__global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
+    k_num_heavy(int64_t nitems, const NumItem *__restrict__ items, const uint32_t *__restrict__ hbits,
+                const int32_t *__restrict__ Bq, const Acc *__restrict__ Bv, const int64_t *__restrict__ At_colptr,
                 const int32_t *__restrict__ At_row, const Acc *__restrict__ At_val,
-                const int32_t *__restrict__ split, int T, int R, int cap, const int64_t *__restrict__ Ccolptr,
-                OutIdx *__restrict__ Crow, Acc *__restrict__ Cval, int *err, unsigned long long *next) {
+                const int32_t *__restrict__ split, int T, int R, int cap, OutIdx *__restrict__ Crow,
+                Acc *__restrict__ Cval, int *err, unsigned long long *next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RW = R >> 5;
     CtaBatch<Acc> &sb = *(CtaBatch<Acc> *)smem_raw;
@@ -113,66 +141,90 @@ __global__ void __launch_bounds__(kBatch)
     __shared__ int wsum[33];
     __shared__ int bad_sh;
     __shared__ long long claim;
-    if (threadIdx.x == 0) bad_sh = 0;
-    for (int64_t it = cta_claim(next, &claim); it < nitems; it = cta_claim(next, &claim)) {
-        const int r0 = num_rec0[it], nr = num_nrec[it];
-        const int j = rec_col[r0], t0 = rec_slab[r0];
+    __shared__ NumItem hdr;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        bad_sh = 0;
+        const long long it = (long long)atomicAdd(next, 1ull);
+        claim = it;
+        if (it < nitems) hdr = items[it];
+    }
+    __syncthreads();
+    for (;;) {
+        const int64_t it = claim;
+        if (it >= nitems) break;
+        const NumItem h = hdr;
+        unsigned long long nxt = 0;
+        if (tid == 0) nxt = atomicAdd(next, 1ull);
+        const int t0 = h.t0, nr = h.nr;
         const int nwords = nr * RW;
-        const uint32_t *src = hbits + (int64_t)r0 * RW;
-        for (int w = threadIdx.x; w < nwords; w += blockDim.x) bp[w].x = src[w];
+        auto seg = [&](int64_t p, long long &st, int &len, Acc &bv) {
+            int q = Bq[p];
+            if (q >= 0) {
+                const int32_t *sp = split + (int64_t)q * (T + 1);
+                int a = sp[t0], b = sp[t0 + nr];
+                st = At_colptr[q] + a;
+                len = b - a;
+                bv = Bv[p];
+            }
+        };
+        const SegReg<Acc> first = cta_first_seg<Acc>(h.p0, h.p1, seg);
+        const uint32_t *src = hbits + (int64_t)h.r0 * RW;
+        for (int w = tid; w < nwords; w += blockDim.x) bp[w].x = src[w];
         __syncthreads();
         const int cnt = cta_scan_popc_packed(bp, nwords, wsum);
-        int want = 0;
-        for (int rr = 0; rr < nr; rr++) want += rec_cnt[r0 + rr];
-        if (cnt != want || cnt > cap) {
-            // the item's room in C was sized from rec_cnt: never write past it
-            if (threadIdx.x == 0) bad_sh = 1;
+        NumItem nh;
+        if (cnt == h.cnt && cnt <= cap) {
+            for (int i = tid; i < cnt; i += blockDim.x) acc[i] = Acc(0);
             __syncthreads();
-            continue;
-        }
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) acc[i] = Acc(0);
-        __syncthreads();
-        const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
-        const int wbase = t0 * RW;
-        bool miss = false;
-        cta_products<true, SPG_NUM_UNROLL, Acc>(
-            p0, p1, sb, At_row, At_val,
-            [&](int64_t p, long long &st, int &len, Acc &bv) {
-                int q = Bq[p];
-                if (q >= 0) {
-                    const int32_t *sp = split + (int64_t)q * (T + 1);
-                    int a = sp[t0], b = sp[t0 + nr];
-                    st = At_colptr[q] + a;
-                    len = b - a;
-                    bv = Bv[p];
+            const int wbase = t0 * RW;
+            bool miss = false;
+            cta_products<true, SPG_NUM_UNROLL, Acc>(
+                h.p0, h.p1, sb, At_row, At_val, first, seg,
+                [&](int r, Acc v) {
+                    // a row missing from the symbolic bitmap (never expected) goes
+                    // to the dump slot acc[cap] and is reported
+                    const uint2 x = bp[(r >> 5) - wbase];
+                    const uint32_t sh = r & 31;
+                    const bool hit = (x.x >> sh) & 1u;
+                    miss |= !hit;
+                    atomic_add_acc(acc + (hit ? (int)(x.y + __popc(x.x & ((1u << sh) - 1u))) : cap), v);
+                });
+            if (miss) bad_sh = 1;
+            if (tid == 0 && (long long)nxt < nitems) nh = items[nxt];
+            // cta_products ends with a barrier: acc is complete
+            for (int i = tid; i < cnt; i += blockDim.x) Cval[h.cbase + i] = acc[i];
+            __syncthreads();
+            // the row ids go to shared memory by rank first (over the consumed
+            // values: cnt ints fit in cnt Accs), then to C in one coalesced run
+            int32_t *srow = (int32_t *)acc;
+            for (int w = tid; w < nwords; w += blockDim.x) {
+                uint32_t word = bp[w].x;
+                int pos = (int)bp[w].y;
+                while (word) {
+                    int bb = __ffs(word) - 1;
+                    srow[pos++] = w * 32 + bb;
+                    word &= word - 1u;
                 }
-            },
-            [&](int r, Acc v) {
-                // a row missing from the symbolic bitmap (never expected) goes to
-                // the dump slot acc[cap] and is reported
-                const uint2 x = bp[(r >> 5) - wbase];
-                const uint32_t sh = r & 31;
-                const bool hit = (x.x >> sh) & 1u;
-                miss |= !hit;
-                atomic_add_acc(acc + (hit ? (int)(x.y + __popc(x.x & ((1u << sh) - 1u))) : cap), v);
-            });
-        if (miss) bad_sh = 1;
-        // cta_products ends with a barrier: acc is complete
-        const int64_t base = Ccolptr[j] + rec_off[r0];
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) Cval[base + i] = acc[i];
-        const int64_t rbase = (int64_t)t0 * R;
-        for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
-            uint32_t word = bp[w].x;
-            int64_t pos = base + bp[w].y;
-            while (word) {
-                int bb = __ffs(word) - 1;
-                Crow[pos++] = (OutIdx)(rbase + w * 32 + bb);
-                word &= word - 1u;
             }
+            __syncthreads();
+            const int64_t rbase = (int64_t)t0 * R;
+            for (int i = tid; i < cnt; i += blockDim.x) Crow[h.cbase + i] = (OutIdx)(rbase + srow[i]);
+        } else {
+            // the item's room in C was sized from the record counts: never
+            // write past it
+            if (tid == 0) {
+                bad_sh = 1;
+                if ((long long)nxt < nitems) nh = items[nxt];
+            }
+        }
+        if (tid == 0) {
+            claim = (long long)nxt;
+            if ((long long)nxt < nitems) hdr = nh;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && bad_sh) atomicOr(err, kDevErrInternal);
+    if (tid == 0 && bad_sh) atomicOr(err, kDevErrInternal);
 }
 
 __global__ void k_rebin_numeric(const int8_t *bin_sym, const int64_t *nnzcol, int64_t n, int8_t *bin_num) {
@@ -240,13 +292,18 @@ static spg_status numeric_typed(spg_plan *p, spg_csc *C) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
         if (occ < 1) occ = 1;
         int g = grid_for(p->nnum, 1, p->sm_count * occ);
+        if (!p->num_items) p->num_items = ws_alloc(p, sizeof(NumItem) * (size_t)p->nnum);
+        NumItem *items = (NumItem *)p->num_items;
+        if (!items) return SPG_OUT_OF_MEMORY;
         s = cuda_check(cudaMemsetAsync(p->d_cnt + kCntNumNextSlot, 0, sizeof(int64_t), p->st), "memset");
         if (s) return s;
         group_begin(p, kKNumHeavy);
-        launch(p, kern, g, threads, smem, p->nnum, p->num_rec0, p->num_nrec, p->rec_col, p->rec_slab, p->rec_cnt,
-               p->rec_off, p->hbits, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv,
-               p->At_colptr, p->At_row, (const Acc *)p->At_val, p->split, p->T, p->R, p->num_cap, p->Ccolptr,
-               (OutIdx *)C->rowidx, (Acc *)C->vals, p->d_err, (unsigned long long *)(p->d_cnt + kCntNumNextSlot));
+        launch(p, k_num_headers, grid_for(p->nnum, 256, p->sm_count * 8), 256, 0, p->nnum, p->num_rec0, p->num_nrec,
+               p->rec_col, p->rec_slab, p->rec_cnt, p->rec_off, p->B.colptr, p->B.ptr_type == SPG_IDX_I64,
+               p->Ccolptr, items);
+        launch(p, kern, g, threads, smem, p->nnum, items, p->hbits, p->Bq, (const Acc *)p->Bv, p->At_colptr,
+               p->At_row, (const Acc *)p->At_val, p->split, p->T, p->R, p->num_cap, (OutIdx *)C->rowidx,
+               (Acc *)C->vals, p->d_err, (unsigned long long *)(p->d_cnt + kCntNumNextSlot));
         group_end(p, kKNumHeavy);
         s = cuda_check(cudaGetLastError(), "numeric heavy");
     }

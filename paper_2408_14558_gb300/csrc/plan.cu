@@ -859,7 +859,7 @@ extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_
     p->out_idx64 = A->idx_type == SPG_IDX_I64;
     p->light_max = lm;
     p->R = R;
-    p->num_cap = R > 4096 ? R : 4096;  // one base slab always fits a numeric item
+    p->num_cap = R > kNumCapMin ? R : kNumCapMin;  // one base slab always fits a numeric item
     p->sym_max_recs = kSymMaxWords / (R / 32);
     p->num_max_recs = kNumMaxWords / (R / 32);
     int dev = 0;

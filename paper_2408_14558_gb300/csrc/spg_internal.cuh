@@ -116,6 +116,7 @@ struct spg_plan {
     int64_t nnzC = -1;
     bool symbolic_done = false;
     int32_t *nbinlist = nullptr;
+    void *num_items = nullptr;  // one header per numeric item (k_num_heavy)
     int64_t nbin_off[spg::kNumBins + 1] = {0};
 
     spg_stats stats{};
@@ -266,9 +267,25 @@ __device__ __forceinline__ void warp_products(int64_t p0, int64_t p1, int lane, 
 
 // Heavy items: the rows of a symbolic item have their bitmap in shared memory
 // (at most kSymMaxWords words = 262,144 rows), those of a numeric item their
-// packed (bitmap word, prefix) pairs (at most kNumMaxWords = 131,072 rows).
+// packed (bitmap word, prefix) pairs (at most kNumMaxWords words = 65,536
+// rows by default: a small table lets four numeric CTAs share an SM).
 constexpr int kSymMaxWords = 8192;
-constexpr int kNumMaxWords = 4096;
+#ifndef SPG_NUM_MAX_WORDS
+#define SPG_NUM_MAX_WORDS 2048
+#endif
+constexpr int kNumMaxWords = SPG_NUM_MAX_WORDS;
+// Smallest entry capacity of a numeric item (the capacity is max(this, R) so
+// that one base slab always fits).
+#ifndef SPG_NUM_CAP_MIN
+#define SPG_NUM_CAP_MIN 4096
+#endif
+constexpr int kNumCapMin = SPG_NUM_CAP_MIN;
+// Minimum resident CTAs per SM asked of the compiler for k_num_heavy: four
+// (60 registers a thread) fill the register file and the shared memory of an
+// SM with the default table; more CTAs hide more of the kernel's latency.
+#ifndef SPG_NUM_MINB
+#define SPG_NUM_MINB 4
+#endif
 // Chunks of 32 products each warp keeps in flight in the heavy kernels
 // (compile-time tuning knobs).
 #ifndef SPG_NUM_UNROLL

@@ -69,21 +69,22 @@ __global__ void __launch_bounds__(kBatch)
         const int r0 = sym_rec0[it], nr = sym_nrec[it];
         const int j = rec_col[r0], t0 = rec_slab[r0];
         const int nwords = nr * RW;
+        const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
+        auto seg = [&](int64_t p, long long &st, int &len, long long &) {
+            int q = Bq[p];
+            if (q >= 0) {
+                const int32_t *sp = split + (int64_t)q * (T + 1);
+                int a = sp[t0], b = sp[t0 + nr];
+                st = At_colptr[q] + a;
+                len = b - a;
+            }
+        };
+        const SegReg<long long> first = cta_first_seg<long long>(p0, p1, seg);
         for (int w = threadIdx.x; w < nwords; w += blockDim.x) bits[w] = 0;
         __syncthreads();
-        const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
         const int wbase = t0 * RW;
         cta_products<false, SPG_SYM_UNROLL, long long>(
-            p0, p1, sb, At_row, (const long long *)nullptr,
-            [&](int64_t p, long long &st, int &len, long long &) {
-                int q = Bq[p];
-                if (q >= 0) {
-                    const int32_t *sp = split + (int64_t)q * (T + 1);
-                    int a = sp[t0], b = sp[t0 + nr];
-                    st = At_colptr[q] + a;
-                    len = b - a;
-                }
-            },
+            p0, p1, sb, At_row, (const long long *)nullptr, first, seg,
             [&](int r, long long) { atomicOr(bits + ((r >> 5) - wbase), 1u << (r & 31)); });
         // cta_products ends with a barrier: the bitmap is complete
         uint32_t *dst = hbits + (int64_t)r0 * RW;
