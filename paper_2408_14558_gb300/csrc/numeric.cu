@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(WARPS * 32)
         if ((int64_t)nout != Ccolptr[j + 1] - base) full = true;
         else
             for (int s = lane; s < nout; s += 32) {
-                Crow[base + s] = (OutIdx)keys[s];
-                Cval[base + s] = vals[s];
+                st_stream(Crow + base + s, (OutIdx)keys[s]);
+                st_stream(Cval + base + s, vals[s]);
             }
         if (__any_sync(kFull, full) && lane == 0) atomicOr(err, kDevErrInternal);
         __syncwarp();
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
         };
         const SegReg<Acc> first = cta_first_seg<Acc>(h.p0, h.p1, seg);
         const uint32_t *src = hbits + (int64_t)h.r0 * RW;
-        for (int w = tid; w < nwords; w += blockDim.x) bp[w].x = src[w];
+        for (int w = tid; w < nwords; w += blockDim.x) bp[w].x = ld_stream(src + w);
         __syncthreads();
         const int cnt = cta_scan_popc_packed(bp, nwords, wsum);
         NumItem nh;
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
             if (miss) bad_sh = 1;
             if (tid == 0 && (long long)nxt < nitems) nh = items[nxt];
             // cta_products ends with a barrier: acc is complete
-            for (int i = tid; i < cnt; i += blockDim.x) Cval[h.cbase + i] = acc[i];
+            for (int i = tid; i < cnt; i += blockDim.x) st_stream(Cval + h.cbase + i, acc[i]);
             __syncthreads();
             // the row ids go to shared memory by rank first (over the consumed
             // values: cnt ints fit in cnt Accs), then to C in one coalesced run
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
             }
             __syncthreads();
             const int64_t rbase = (int64_t)t0 * R;
-            for (int i = tid; i < cnt; i += blockDim.x) Crow[h.cbase + i] = (OutIdx)(rbase + srow[i]);
+            for (int i = tid; i < cnt; i += blockDim.x) st_stream(Crow + h.cbase + i, (OutIdx)(rbase + srow[i]));
         } else {
             // the item's room in C was sized from the record counts: never
             // write past it

@@ -269,7 +269,19 @@ __device__ __forceinline__ void warp_products(int64_t p0, int64_t p1, int lane, 
 // (at most kSymMaxWords words = 262,144 rows), those of a numeric item their
 // packed (bitmap word, prefix) pairs (at most kNumMaxWords words = 65,536
 // rows by default: a small table lets four numeric CTAs share an SM).
-constexpr int kSymMaxWords = 8192;
+#ifndef SPG_SYM_MAX_WORDS
+#define SPG_SYM_MAX_WORDS 8192
+#endif
+constexpr int kSymMaxWords = SPG_SYM_MAX_WORDS;
+// Launch bound of k_sym_heavy: 0 gives the compiler only the CTA size.
+#ifndef SPG_SYM_MINB
+#define SPG_SYM_MINB 0
+#endif
+#if SPG_SYM_MINB > 0
+#define SPG_SYM_BOUNDS __launch_bounds__(kBatch, SPG_SYM_MINB)
+#else
+#define SPG_SYM_BOUNDS __launch_bounds__(kBatch)
+#endif
 #ifndef SPG_NUM_MAX_WORDS
 #define SPG_NUM_MAX_WORDS 2048
 #endif
@@ -280,6 +292,29 @@ constexpr int kNumMaxWords = SPG_NUM_MAX_WORDS;
 #define SPG_NUM_CAP_MIN 4096
 #endif
 constexpr int kNumCapMin = SPG_NUM_CAP_MIN;
+// C and the heavy bitmaps pass through L2 once; storing (and reading the
+// bitmaps) with the evict-first hint keeps A~, which the products re-read,
+// resident instead.
+#ifndef SPG_STREAM_HINTS
+#define SPG_STREAM_HINTS 1
+#endif
+template <typename T>
+__device__ __forceinline__ void st_stream(T *p, T v) {
+#if SPG_STREAM_HINTS
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T *p) {
+#if SPG_STREAM_HINTS
+    return __ldcs(p);
+#else
+    return *p;
+#endif
+}
+
 // Minimum resident CTAs per SM asked of the compiler for k_num_heavy: four
 // (60 registers a thread) fill the register file and the shared memory of an
 // SM with the default table; more CTAs hide more of the kernel's latency.

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 // One CTA per symbolic item: records [r0, r0 + nr) of one heavy column, i.e.
 // base slabs t0 .. t0 + nr - 1.  Every product sets its row's bit; then the
 // bitmap of each record and its population count are stored.
-__global__ void __launch_bounds__(kBatch)
+__global__ void SPG_SYM_BOUNDS
     k_sym_heavy(int64_t nitems, const int32_t *__restrict__ sym_rec0, const int32_t *__restrict__ sym_nrec,
                 const int32_t *__restrict__ rec_col, const int32_t *__restrict__ rec_slab, const void *Bcolptr,
                 int p64, const int32_t *__restrict__ Bq, const int64_t *__restrict__ At_colptr,
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kBatch)
             [&](int r, long long) { atomicOr(bits + ((r >> 5) - wbase), 1u << (r & 31)); });
         // cta_products ends with a barrier: the bitmap is complete
         uint32_t *dst = hbits + (int64_t)r0 * RW;
-        for (int w = threadIdx.x; w < nwords; w += blockDim.x) dst[w] = bits[w];
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) st_stream(dst + w, bits[w]);
         for (int rr = wid; rr < nr; rr += nw) {
             int c = 0;
             for (int w = lane; w < RW; w += 32) c += __popc(bits[rr * RW + w]);
