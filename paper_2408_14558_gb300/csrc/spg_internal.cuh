@@ -315,6 +315,12 @@ __device__ __forceinline__ T ld_stream(const T *p) {
 #endif
 }
 
+// k_num_heavy writes an item's row ids right after its bitmap scan (1) or
+// stages them in shared memory after the products (0).
+#ifndef SPG_EARLY_ROWS
+#define SPG_EARLY_ROWS 0
+#endif
+
 // Minimum resident CTAs per SM asked of the compiler for k_num_heavy: four
 // (60 registers a thread) fill the register file and the shared memory of an
 // SM with the default table; more CTAs hide more of the kernel's latency.
