@@ -7,11 +7,13 @@
 //                    column its place in D~ (Algorithm 1, D~ = H_i AND D)
 //   k_dtilde         the ascending list D~_i
 //   k_fetch          Algorithm 2 with groups of b consecutive column ids
-//   k_gather_len / k_gather_copy   A~_i = A(:, D~_i); one CTA per chosen fetch
-//                    block (the single-GPU analogue of one MPI_Get per group)
+//   k_gather_len / k_gather_shift / k_gather_copy   A~_i = A(:, D~_i) for all
+//                    blocks in one entry-balanced copy (on one GPU the chosen
+//                    fetch blocks only give the volume Algorithm 2 transfers)
 //   k_remap_B        B_i's rows k -> column of A~_i (Algorithm 1's local index)
 //   k_col_stats      flops_j (Section 3.2), row window, features, bin id
 //   k_split          heavy bins: per A~ column, the first entry of every row slab
+#include <algorithm>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -267,32 +269,67 @@ __device__ __forceinline__ long long load_val<long long>(const void *v, int vt, 
     return vt == SPG_VAL_I32 ? (long long)__ldg((const int *)v + i) : (long long)__ldg((const long long *)v + i);
 }
 
-// One CTA per chosen fetch block (i, t): copy the required columns it holds
-// into A~ (rows narrowed to int32, values widened to the accumulation type).
+// Per A~ column g: the entry e of A~ sits at position e + shift[g] of A.
+__global__ void k_gather_shift(const int32_t *dtilde, int64_t ndt, const void *Acolptr, int p64,
+                               const int64_t *At_colptr, int64_t *shift) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ndt; g += (int64_t)gridDim.x * blockDim.x)
+        shift[g] = ld_ptr(Acolptr, p64, dtilde[g]) - At_colptr[g];
+}
+
+// A~ = A(:, D~) for all blocks at once (rows narrowed to int32, values widened
+// to the accumulation type), balanced by entries: warp w copies the entries
+// [w * chunk, (w + 1) * chunk) of A~.  It finds the column of its first entry
+// by a 32-way search of At_colptr, then walks 32 entries a step; every A~
+// column is non-empty (D~ is a subset of D), so the column starts inside a
+// step mark distinct positions and one warp OR-reduction gives each lane its
+// column.
 template <typename Acc>
-__global__ void k_gather_copy(const uint32_t *H, const uint32_t *D, const int64_t *rankpre, int64_t W,
-                              int64_t k, int64_t b, int64_t nfb, int P, const uint8_t *fetch,
-                              const int32_t *dtilde, const void *Acolptr, int p64, const void *Arow,
-                              int i64, const void *Aval, int vt, const int64_t *At_colptr,
-                              int32_t *At_row, Acc *At_val) {
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int64_t units = nfb * P;
-    for (int64_t x = blockIdx.x; x < units; x += gridDim.x) {
-        if (!fetch[x]) continue;
-        int i = (int)(x / nfb);
-        int64_t t = x % nfb;
-        int64_t lo = t * b, hi = min(k, lo + b);
-        int64_t g0 = rank_at(H, D, rankpre, W, i, lo), g1 = rank_at(H, D, rankpre, W, i, hi);
-        for (int64_t g = g0 + wid; g < g1; g += nw) {
-            int64_t h = dtilde[g];
-            int64_t src = ld_ptr(Acolptr, p64, h);
-            int64_t dst = At_colptr[g];
-            int64_t len = At_colptr[g + 1] - dst;
-            for (int64_t e = lane; e < len; e += 32) {
-                At_row[dst + e] = (int32_t)ld_ptr(Arow, i64, src + e);
-                At_val[dst + e] = load_val<Acc>(Aval, vt, src + e);
-            }
+__global__ void k_gather_copy(const int64_t *__restrict__ At_colptr, const int64_t *__restrict__ shift, int64_t ndt,
+                              int64_t nAt, int64_t chunk, const void *Arow, int i64, const void *Aval, int vt,
+                              int32_t *__restrict__ At_row, Acc *__restrict__ At_val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t e0 = w * chunk, e1 = min(nAt, e0 + chunk);
+    if (e0 >= e1) return;  // the whole warp
+    // largest g with At_colptr[g] <= e0, searched in [lo, hi)
+    int64_t lo = 0, hi = ndt;
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t idx = lo + lane * step;
+        const uint32_t b = __ballot_sync(kFull, idx < hi && At_colptr[idx] <= e0);
+        lo += (31 - __clz(b)) * step;  // lane 0 always votes yes
+        hi = min(hi, lo + step);
+    }
+    {
+        const int64_t idx = lo + lane;
+        const uint32_t b = __ballot_sync(kFull, idx < hi && At_colptr[idx] <= e0);
+        lo += 31 - __clz(b);
+    }
+    int64_t s0 = lo;  // the column holding entry f
+    for (int64_t f = e0; f < e1; f += 32) {
+        // lane k holds column s0 + k: its start and its shift
+        const int64_t sk = s0 + lane;
+        const int64_t bk = sk < ndt ? At_colptr[sk] : INT64_MAX;
+        const int64_t shk = sk < ndt ? shift[sk] : 0;
+        const int64_t pos = bk - f;  // >= 1 for k >= 1
+        const uint32_t M = __reduce_or_sync(kFull, (lane > 0 && pos < 32) ? (1u << (int)pos) : 0u);
+        const int k = __popc(M & ((2u << lane) - 1u));
+        const int64_t sh = __shfl_sync(kFull, shk, k);
+        const int64_t e = f + lane;
+        if (e < e1) {
+            const int64_t src = e + sh;
+            At_row[e] = (int32_t)ld_ptr(Arow, i64, src);
+            At_val[e] = load_val<Acc>(Aval, vt, src);
         }
+        // the column holding f + 32
+        int c = __popc(M);
+        int64_t nb;
+        if (c < 31)
+            nb = __shfl_sync(kFull, bk, c + 1);
+        else
+            nb = s0 + 32 < ndt ? At_colptr[s0 + 32] : INT64_MAX;
+        if (nb == f + 32) c++;
+        s0 += c;
     }
 }
 
@@ -660,17 +697,22 @@ static spg_status plan_build(spg_plan *p) {
     p->Bq = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->nnzB + 1));
     p->Bv = ws_alloc(p, accsz * (size_t)(p->nnzB + 1));
     if (!p->At_row || !p->At_val || !p->Bq || !p->Bv) return SPG_OUT_OF_MEMORY;
-    if (P * p->nfb > 0 && p->nAt > 0) {
-        int g = grid_for(P * p->nfb, 1, sm * 8);
+    if (p->ndt > 0 && p->nAt > 0) {
+        int64_t *shift = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)p->ndt);
+        if (!shift) return SPG_OUT_OF_MEMORY;
+        // about 2048 entries per warp, at most 32 CTAs of 8 warps per SM
+        const int64_t warps = std::max<int64_t>(1, std::min<int64_t>((p->nAt + 2047) / 2048, (int64_t)sm * 32 * 8));
+        const int64_t chunk = ((p->nAt + warps - 1) / warps + 31) & ~(int64_t)31;
+        const int64_t g = (((p->nAt + chunk - 1) / chunk) + 7) / 8;
         group_begin(p, kKGather);
+        launch(p, k_gather_shift, grid_for(p->ndt, 256, sm * 8), 256, 0, p->dtilde, p->ndt, A.colptr, p64A,
+               p->At_colptr, shift);
         if (p->acc_f64)
-            launch(p, k_gather_copy<double>, g, 256, 0, p->Hbits, p->Dbits, p->rankpre, W, k, p->b, p->nfb, P,
-                   p->fetch, p->dtilde, A.colptr, p64A, A.rowidx, i64A, A.vals, A.val_type, p->At_colptr,
-                   p->At_row, (double *)p->At_val);
+            launch(p, k_gather_copy<double>, (unsigned)g, 256, 0, p->At_colptr, shift, p->ndt, p->nAt, chunk,
+                   A.rowidx, i64A, A.vals, A.val_type, p->At_row, (double *)p->At_val);
         else
-            launch(p, k_gather_copy<long long>, g, 256, 0, p->Hbits, p->Dbits, p->rankpre, W, k, p->b, p->nfb, P,
-                   p->fetch, p->dtilde, A.colptr, p64A, A.rowidx, i64A, A.vals, A.val_type, p->At_colptr,
-                   p->At_row, (long long *)p->At_val);
+            launch(p, k_gather_copy<long long>, (unsigned)g, 256, 0, p->At_colptr, shift, p->ndt, p->nAt, chunk,
+                   A.rowidx, i64A, A.vals, A.val_type, p->At_row, (long long *)p->At_val);
         group_end(p, kKGather);
         LAUNCH_OK("gather");
     }
