@@ -117,6 +117,7 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
     int *keys_all = (int *)(vals_all + nwarps * S_MAX);
     int *keys = keys_all + wid * S_MAX;
     Acc *vals = vals_all + wid * S_MAX;
+    int *hist = keys_all + nwarps * S_MAX + wid * 256;
     WarpSeg<Acc> &ws = segs[wid];
     while (true) {
         unsigned long long t = 0;
@@ -285,11 +286,7 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
                 if (full || nout != want) {
                     if (lane == 0) atomicOr(err, kDevErrInternal);
                 } else {
-                    int npad = 1;
-                    while (npad < nout) npad <<= 1;
-                    for (int s = nout + lane; s < npad; s += 32) keys[s] = INT32_MAX;
-                    __syncwarp();
-                    warp_bitonic<Acc>(keys, vals, npad, lane);
+                    warp_sort_pairs<Acc>(keys, vals, nout, S, hist, lane);
                     for (int s = lane; s < nout; s += 32) {
                         out_row[base + s] = (OutIdx)keys[s];
                         out_val[base + s] = vals[s];
@@ -507,7 +504,8 @@ extern "C" spg_status spgemm_batch_create(int32_t count, const spg_csc *A, const
     }
     if (!s) {
         const size_t accsz = 8;
-        b->smem = (sizeof(WarpSeg<double>)) * (size_t)b->warps + (accsz + sizeof(int)) * (size_t)b->warps * (1u << kBatchMaxLogS);
+        b->smem = (sizeof(WarpSeg<double>)) * (size_t)b->warps + (accsz + sizeof(int)) * (size_t)b->warps * (1u << kBatchMaxLogS) +
+                  sizeof(int) * 256 * (size_t)b->warps;
         s = f64 ? batch_capture<double, int>(b) : batch_capture<long long, int>(b);
     }
     if (s) {

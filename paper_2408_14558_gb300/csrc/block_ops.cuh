@@ -107,4 +107,115 @@ __device__ __forceinline__ void warp_bitonic(int *keys, Acc *vals, int npad, int
     }
 }
 
+// Sort the pairs (keys[0..n), vals[0..n)) ascending by key with one warp; the
+// keys are distinct and non-negative, and keys/vals are the front of a table of
+// S slots.  n <= 32: one bitonic network across the lanes' registers.
+// n <= S/2: LSD radix sort with 8-bit digits over the bits the largest key
+// uses, ping-ponging between the front and the upper half of the table; each
+// pass is stable because the entries are scattered 32 at a time in order and
+// lanes holding equal digits are ranked by __match_any_sync.  Otherwise the
+// in-place bitonic network above.  hist: 256 ints of this warp.
+template <typename Acc>
+__device__ __forceinline__ void warp_sort_pairs(int *keys, Acc *vals, int n, int S, int *hist, int lane) {
+    if (n <= 1) return;
+    if (n <= 32) {
+        int k = lane < n ? keys[lane] : INT32_MAX;
+        Acc v = lane < n ? vals[lane] : Acc(0);
+#pragma unroll
+        for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                const int ok = __shfl_xor_sync(kFull, k, stride);
+                const Acc ov = __shfl_xor_sync(kFull, v, stride);
+                const bool ascending = (lane & size) == 0;
+                const bool lower = (lane & stride) == 0;
+                // the lower lane of a pair keeps the smaller key in an
+                // ascending block, the larger in a descending one
+                if (lower == ascending ? ok < k : ok > k) {
+                    k = ok;
+                    v = ov;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < n) {
+            keys[lane] = k;
+            vals[lane] = v;
+        }
+        __syncwarp();
+        return;
+    }
+    if (n > (S >> 1)) {
+        int npad = 1;
+        while (npad < n) npad <<= 1;
+        for (int s = n + lane; s < npad; s += 32) keys[s] = INT32_MAX;
+        __syncwarp();
+        warp_bitonic<Acc>(keys, vals, npad, lane);
+        return;
+    }
+    int kmax = 0;
+    for (int s = lane; s < n; s += 32) kmax = max(kmax, keys[s]);
+    kmax = __reduce_max_sync(kFull, kmax);
+    const int bits = 32 - __clz(kmax);
+    int *sk = keys, *dk = keys + (S >> 1);
+    Acc *sv = vals, *dv = vals + (S >> 1);
+    const unsigned below = (1u << lane) - 1u;
+    for (int shift = 0; shift < bits; shift += 8) {
+        for (int i = lane; i < 256; i += 32) hist[i] = 0;
+        __syncwarp();
+        for (int s = lane; s < n; s += 32) atomicAdd(hist + ((sk[s] >> shift) & 255), 1);
+        __syncwarp();
+        // exclusive scan of the 256 counts, 8 consecutive per lane
+        int c[8], tot = 0;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            c[u] = hist[lane * 8 + u];
+            tot += c[u];
+        }
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += x;
+        }
+        int run = incl - tot;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            hist[lane * 8 + u] = run;
+            run += c[u];
+        }
+        __syncwarp();
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const int s = c0 + lane;
+            const bool valid = s < n;
+            const int k = valid ? sk[s] : 0;
+            const Acc v = valid ? sv[s] : Acc(0);
+            const int d = valid ? ((k >> shift) & 255) : 256 + lane;
+            const unsigned peers = __match_any_sync(kFull, d);
+            const int rank = __popc(peers & below);
+            const int pos = valid ? hist[d] + rank : 0;
+            __syncwarp();
+            if (valid) {
+                dk[pos] = k;
+                dv[pos] = v;
+                if (rank == 0) hist[d] += __popc(peers);
+            }
+            __syncwarp();
+        }
+        int *tk = sk;
+        sk = dk;
+        dk = tk;
+        Acc *tv = sv;
+        sv = dv;
+        dv = tv;
+    }
+    if (sk != keys) {
+        for (int s = lane; s < n; s += 32) {
+            keys[s] = sk[s];
+            vals[s] = sv[s];
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace spg

@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int *keys = keys_all + wid * S;
     Acc *vals = vals_all + wid * S;
+    int *hist = keys_all + WARPS * S + wid * 256;
     for (int64_t c = (int64_t)blockIdx.x * WARPS + wid; c < ncols; c += (int64_t)gridDim.x * WARPS) {
         const int j = list[c];
         for (int s = lane; s < S; s += 32) {
@@ -284,11 +285,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         if (full || nout > cap[j]) {
             if (lane == 0) mark_overflow(flag, j, nflag);
         } else {
-            int npad = 1;
-            while (npad < nout) npad <<= 1;
-            for (int s = nout + lane; s < npad; s += 32) keys[s] = INT32_MAX;
-            __syncwarp();
-            warp_bitonic<Acc>(keys, vals, npad, lane);
+            warp_sort_pairs<Acc>(keys, vals, nout, S, hist, lane);
             const int64_t base = capoff[j];
             for (int s = lane; s < nout; s += 32) {
                 trow[base + s] = (OutIdx)keys[s];
@@ -772,7 +769,8 @@ template <int LOGS, int WARPS, typename Acc, typename OutIdx>
 static spg_status launch_light_learned(spg_plan *p, const int32_t *list, int64_t cnt, const int64_t *capoff,
                                        const int64_t *cap, int64_t *nnz, int32_t *flag, unsigned long long *nflag,
                                        void *trow, void *tval) {
-    size_t smem = sizeof(WarpSeg<Acc>) * WARPS + (sizeof(Acc) + sizeof(int)) * (size_t)WARPS * (1 << LOGS);
+    size_t smem = sizeof(WarpSeg<Acc>) * WARPS + (sizeof(Acc) + sizeof(int)) * (size_t)WARPS * (1 << LOGS) +
+                  sizeof(int) * 256 * (size_t)WARPS;
     auto kern = k_light_learned<LOGS, WARPS, Acc, OutIdx>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;

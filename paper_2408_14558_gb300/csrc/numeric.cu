@@ -3,7 +3,7 @@
 // pointers produced by the symbolic pass.
 //   light bins: one warp per column, shared open-addressing table of
 //               (row, value) sized >= 2 x nnz_j; afterwards the occupied slots
-//               are compacted in place and sorted by row (bitonic network)
+//               are compacted in place and sorted by row (warp radix sort)
 //   heavy bin:  one CTA per (column, row slab): the symbolic bitmap of the
 //               slab gives every present row its rank, products accumulate at
 //               acc[rank] in shared memory, and the slab is written out in row
@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int *keys = keys_all + wid * S;
     Acc *vals = vals_all + wid * S;
+    int *hist = keys_all + WARPS * S + wid * 256;
     for (int64_t c = (int64_t)blockIdx.x * WARPS + wid; c < ncols; c += (int64_t)gridDim.x * WARPS) {
         const int j = list[c];
         for (int s = lane; s < S; s += 32) {
@@ -73,18 +74,16 @@ __global__ void __launch_bounds__(WARPS * 32)
             nout += __popc(bal);
             __syncwarp();
         }
-        int npad = 1;
-        while (npad < nout) npad <<= 1;
-        for (int s = nout + lane; s < npad; s += 32) keys[s] = INT32_MAX;
-        __syncwarp();
-        warp_bitonic<Acc>(keys, vals, npad, lane);
         const int64_t base = Ccolptr[j];
-        if ((int64_t)nout != Ccolptr[j + 1] - base) full = true;
-        else
+        if ((int64_t)nout != Ccolptr[j + 1] - base) {
+            full = true;
+        } else {
+            warp_sort_pairs<Acc>(keys, vals, nout, S, hist, lane);
             for (int s = lane; s < nout; s += 32) {
                 st_stream(Crow + base + s, (OutIdx)keys[s]);
                 st_stream(Cval + base + s, vals[s]);
             }
+        }
         if (__any_sync(kFull, full) && lane == 0) atomicOr(err, kDevErrInternal);
         __syncwarp();
     }
@@ -268,7 +267,8 @@ __global__ void k_rebin_numeric(const int8_t *bin_sym, const int64_t *nnzcol, in
 
 template <int LOGS, int WARPS, typename Acc, typename OutIdx>
 static spg_status launch_num_light(spg_plan *p, const int32_t *list, int64_t cnt, spg_csc *C) {
-    size_t smem = sizeof(WarpSeg<Acc>) * WARPS + (sizeof(Acc) + sizeof(int)) * (size_t)WARPS * (1 << LOGS);
+    size_t smem = sizeof(WarpSeg<Acc>) * WARPS + (sizeof(Acc) + sizeof(int)) * (size_t)WARPS * (1 << LOGS) +
+                  sizeof(int) * 256 * (size_t)WARPS;
     auto kern = k_num_light<LOGS, WARPS, Acc, OutIdx>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
