@@ -137,14 +137,9 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
         if (!numeric) {
             for (int j = tk.c0; j < tk.c1; j++) {
                 const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
-                // table size from this column's bound min(flops, m)
-                long long fl = 0;
-                for (int64_t p = p0 + lane; p < p1; p += 32) {
-                    const int k = in.Brow[p];
-                    fl += ld_ptr(in.Acp, in.acp64, k + 1) - ld_ptr(in.Acp, in.acp64, k);
-                }
-                fl = warp_sum_ll(fl);
-                const int logS = log_table(min(fl, (long long)in.m));
+                // the largest table: the column's bound min(flops, m) <= S_MAX / 2
+                // needs no pass of its own
+                const int logS = kBatchMaxLogS;
                 const int S = 1 << logS;
                 for (int s = lane; s < S; s += 32) keys[s] = kEmptyKey;
                 __syncwarp();
@@ -226,46 +221,18 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
                 }
                 __syncwarp();
                 bool full = false;
-                // A's values may be stored as double, int32 or int64: load them here
-                {
-                    for (int64_t b0 = p0; b0 < p1; b0 += 32) {
-                        const int64_t p = b0 + lane;
-                        long long st = 0;
-                        int len = 0;
-                        Acc bv = Acc(0);
-                        if (p < p1) seg(p, st, len, bv);
-                        int incl = len;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            int x = __shfl_up_sync(kFull, incl, o);
-                            if (lane >= o) incl += x;
-                        }
-                        const int total = __shfl_sync(kFull, incl, 31);
-                        ws.pref[lane] = incl - len;
-                        ws.start[lane] = st;
-                        ws.bv[lane] = bv;
-                        __syncwarp();
-                        for (int f0 = 0; f0 < total; f0 += 32) {
-                            const int fi = f0 + lane;
-                            if (fi < total) {
-                                int s = 0;
-#pragma unroll
-                                for (int stp = 16; stp > 0; stp >>= 1)
-                                    if (ws.pref[s + stp] <= fi) s += stp;
-                                const long long e = ws.start[s] + (fi - ws.pref[s]);
-                                const int r = __ldg(in.Arow + e);
-                                const Acc v = mul_acc<Acc>(bval_load<Acc>(in.Aval, in.vt, e), ws.bv[s]);
-                                bool fresh;
-                                const int slot = hash_insert(keys, logS, r, &fresh);
-                                if (slot < 0)
-                                    full = true;
-                                else
-                                    atomic_add_acc(vals + slot, v);
-                            }
-                        }
-                        __syncwarp();
-                    }
-                }
+                // A's values may be stored as double, int32 or int64
+                warp_products_v<true, 4, Acc>(
+                    p0, p1, lane, ws, in.Arow, seg,
+                    [&](long long e) { return bval_load<Acc>(in.Aval, in.vt, e); },
+                    [&](int r, Acc v) {
+                        bool fresh;
+                        const int slot = hash_insert(keys, logS, r, &fresh);
+                        if (slot < 0)
+                            full = true;
+                        else
+                            atomic_add_acc(vals + slot, v);
+                    });
                 __syncwarp();
                 int nout = 0;
                 for (int c0 = 0; c0 < S; c0 += 32) {

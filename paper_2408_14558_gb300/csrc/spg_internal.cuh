@@ -222,13 +222,15 @@ struct WarpSeg {
 
 // Walk every product of the B' entries [p0, p1) of one output column with a
 // whole warp.  seg(p, start, len, bv) gives the A~ positions [start, start+len)
-// that B' entry p multiplies and its value.  The lengths of 32 consecutive
-// entries are prefix-summed so that all 32 lanes stay busy however short the
-// segments are; body(row, product) is called once per product.
-template <bool NEED_VAL, typename Acc, typename SegFn, typename Body>
-__device__ __forceinline__ void warp_products(int64_t p0, int64_t p1, int lane, WarpSeg<Acc> &ws,
-                                              const int32_t *__restrict__ At_row,
-                                              const Acc *__restrict__ At_val, SegFn seg, Body body) {
+// that B' entry p multiplies and its value; aval(e) loads A~'s value e.  The
+// lengths of 32 consecutive entries are prefix-summed so that all 32 lanes stay
+// busy however short the segments are; each step locates and loads U windows
+// of 32 products before any of them is used, so that U loads per lane are in
+// flight.  body(row, product) is called once per product.
+template <bool NEED_VAL, int U, typename Acc, typename SegFn, typename ValFn, typename Body>
+__device__ __forceinline__ void warp_products_v(int64_t p0, int64_t p1, int lane, WarpSeg<Acc> &ws,
+                                                const int32_t *__restrict__ At_row, SegFn seg, ValFn aval,
+                                                Body body) {
     for (int64_t base = p0; base < p1; base += 32) {
         int64_t p = base + lane;
         long long st = 0;
@@ -246,23 +248,45 @@ __device__ __forceinline__ void warp_products(int64_t p0, int64_t p1, int lane, 
         ws.start[lane] = st;
         if (NEED_VAL) ws.bv[lane] = bv;
         __syncwarp();
-        for (int f0 = 0; f0 < total; f0 += 32) {
-            int fi = f0 + lane;
-            if (fi < total) {
-                int s = 0;
+        for (int f0 = 0; f0 < total; f0 += 32 * U) {
+            int r[U];
+            Acc a[U], b[U];
+            bool ok[U];
 #pragma unroll
-                for (int stp = 16; stp > 0; stp >>= 1)
-                    if (ws.pref[s + stp] <= fi) s += stp;
-                long long e = ws.start[s] + (fi - ws.pref[s]);
-                int r = __ldg(At_row + e);
-                if (NEED_VAL)
-                    body(r, mul_acc<Acc>(__ldg(At_val + e), ws.bv[s]));
-                else
-                    body(r, Acc(0));
+            for (int u = 0; u < U; u++) {
+                const int fi = f0 + 32 * u + lane;
+                ok[u] = fi < total;
+                r[u] = 0;
+                a[u] = Acc(0);
+                b[u] = Acc(0);
+                if (ok[u]) {
+                    int s = 0;
+#pragma unroll
+                    for (int stp = 16; stp > 0; stp >>= 1)
+                        if (ws.pref[s + stp] <= fi) s += stp;
+                    const long long e = ws.start[s] + (fi - ws.pref[s]);
+                    r[u] = __ldg(At_row + e);
+                    if (NEED_VAL) {
+                        a[u] = aval(e);
+                        b[u] = ws.bv[s];
+                    }
+                }
             }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (ok[u]) body(r[u], NEED_VAL ? mul_acc<Acc>(a[u], b[u]) : Acc(0));
         }
         __syncwarp();
     }
+}
+
+// The same walk over A~ values stored in the accumulation type.
+template <bool NEED_VAL, typename Acc, typename SegFn, typename Body>
+__device__ __forceinline__ void warp_products(int64_t p0, int64_t p1, int lane, WarpSeg<Acc> &ws,
+                                              const int32_t *__restrict__ At_row,
+                                              const Acc *__restrict__ At_val, SegFn seg, Body body) {
+    warp_products_v<NEED_VAL, 4, Acc>(
+        p0, p1, lane, ws, At_row, seg, [&](long long e) { return __ldg(At_val + e); }, body);
 }
 
 // Heavy items: the rows of a symbolic item have their bitmap in shared memory
