@@ -50,6 +50,11 @@ struct BatchTask {
 };
 
 constexpr int kBatchMaxLogS = 11;  // per-warp tables of up to 2048 slots
+// Instances are launched in three classes by the table their largest column
+// needs (up to 512, 1024 and 2048 slots), each class by its own persistent
+// kernel, so that small tables buy more resident warps.
+constexpr int kBatchClasses = 3;
+constexpr int kBatchClassLogS[kBatchClasses] = {9, 10, 11};
 enum : int { kBatchErrTimeout = 8 };
 
 template <typename Acc>
@@ -104,13 +109,13 @@ __device__ __forceinline__ int log_table(long long U) {
     return l;
 }
 
-template <typename Acc, typename OutIdx>
+template <int LOGS_MAX, typename Acc, typename OutIdx>
 __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const BatchTask *__restrict__ tasks,
                                    int64_t ntasks, unsigned long long *head, int *sym_done, int *ready,
                                    int64_t *nnz, int64_t *colptr, OutIdx *__restrict__ out_row,
                                    Acc *__restrict__ out_val, int *err, long long timeout_ns, int stall_inst) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int S_MAX = 1 << kBatchMaxLogS;
+    constexpr int S_MAX = 1 << LOGS_MAX;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     WarpSeg<Acc> *segs = (WarpSeg<Acc> *)smem_raw;
     Acc *vals_all = (Acc *)(segs + nwarps);
@@ -137,9 +142,9 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
         if (!numeric) {
             for (int j = tk.c0; j < tk.c1; j++) {
                 const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
-                // the largest table: the column's bound min(flops, m) <= S_MAX / 2
-                // needs no pass of its own
-                const int logS = kBatchMaxLogS;
+                // the class's largest table: every column's bound min(flops, m)
+                // is <= S_MAX / 2, so it needs no pass of its own
+                const int logS = LOGS_MAX;
                 const int S = 1 << logS;
                 for (int s = lane; s < S; s += 32) keys[s] = kEmptyKey;
                 __syncwarp();
@@ -285,6 +290,7 @@ struct spg_batch {
     void *out_row = nullptr, *out_val = nullptr;
     int grid = 0, warps = 8;
     size_t smem = 0;
+    int64_t class_off[spg::kBatchClasses + 1] = {};  // tasks of class c: [class_off[c], class_off[c + 1])
     int sm_count = 0;
 };
 
@@ -322,29 +328,46 @@ extern "C" spg_status spgemm_batch_destroy(spg_batch *b) {
     return SPG_OK;
 }
 
-template <typename Acc, typename OutIdx>
-static spg_status batch_capture(spg_batch *b) {
-    auto kern = k_batch_persistent<Acc, OutIdx>;
-    spg_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem),
+template <int LOGS_MAX, typename Acc, typename OutIdx>
+static spg_status batch_launch_class(spg_batch *b, int c) {
+    const int64_t t0 = b->class_off[c], nt = b->class_off[c + 1] - t0;
+    if (nt == 0) return SPG_OK;
+    auto kern = k_batch_persistent<LOGS_MAX, Acc, OutIdx>;
+    const size_t smem = sizeof(WarpSeg<double>) * (size_t)b->warps +
+                        (8 + sizeof(int)) * (size_t)b->warps * (1u << LOGS_MAX) + sizeof(int) * 256 * (size_t)b->warps;
+    spg_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                               "batch smem");
     if (s) return s;
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, b->warps * 32, b->smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, b->warps * 32, smem);
     if (occ < 1) {
         set_error("batch kernel does not fit on an SM with %d warps", b->warps);
         return SPG_UNSUPPORTED;
     }
-    b->grid = b->sm_count * occ;
-    s = cuda_check(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
-    if (s) return s;
-    cudaMemsetAsync(b->head, 0, sizeof(unsigned long long), b->cap_stream);
-    cudaMemsetAsync(b->sym_done, 0, sizeof(int) * (size_t)b->count * 2 + sizeof(int) * 4, b->cap_stream);
-    kern<<<b->grid, b->warps * 32, b->smem, b->cap_stream>>>(
-        b->insts, b->tasks, b->ntasks, b->head, b->sym_done, b->ready, b->nnz, b->colptr, (OutIdx *)b->out_row,
+    const int grid = b->sm_count * occ;
+    b->grid = std::max(b->grid, grid);
+    b->smem = std::max(b->smem, smem);
+    kern<<<grid, b->warps * 32, smem, b->cap_stream>>>(
+        b->insts, b->tasks + t0, nt, b->head + c, b->sym_done, b->ready, b->nnz, b->colptr, (OutIdx *)b->out_row,
         (Acc *)b->out_val, b->err, b->opt.timeout_ns, b->opt.stall_instance);
-    cudaError_t le = cudaGetLastError();
-    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &b->graph);
-    if (le != cudaSuccess) return cuda_check(le, "batch kernel launch");
+    return cuda_check(cudaGetLastError(), "batch kernel launch");
+}
+
+// One graph: clear the counters and flags, then the class kernels in turn.
+template <typename Acc, typename OutIdx>
+static spg_status batch_capture(spg_batch *b) {
+    spg_status s = cuda_check(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
+    if (s) return s;
+    cudaMemsetAsync(b->head, 0, sizeof(unsigned long long) * kBatchClasses, b->cap_stream);
+    cudaMemsetAsync(b->sym_done, 0, sizeof(int) * (size_t)b->count * 2 + sizeof(int) * 4, b->cap_stream);
+    static_assert(kBatchClasses == 3, "one launch per class below");
+    s = batch_launch_class<kBatchClassLogS[0], Acc, OutIdx>(b, 0);
+    if (!s) s = batch_launch_class<kBatchClassLogS[1], Acc, OutIdx>(b, 1);
+    if (!s) s = batch_launch_class<kBatchClassLogS[2], Acc, OutIdx>(b, 2);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    b->graph = g;
+    if (s) return s;
     s = cuda_check(e, "end capture");
     if (s) return s;
     return cuda_check(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
@@ -418,7 +441,7 @@ extern "C" spg_status spgemm_batch_create(int32_t count, const spg_csc *A, const
     if (!s) {
         b->insts = (BatchInst *)batch_alloc(b, sizeof(BatchInst) * (size_t)count);
         b->tasks = (BatchTask *)batch_alloc(b, sizeof(BatchTask) * (size_t)b->ntasks);
-        b->head = (unsigned long long *)batch_alloc(b, sizeof(unsigned long long));
+        b->head = (unsigned long long *)batch_alloc(b, sizeof(unsigned long long) * kBatchClasses);
         b->sym_done = (int *)batch_alloc(b, sizeof(int) * (size_t)count * 2 + sizeof(int) * 4);
         b->nnz = (int64_t *)batch_alloc(b, sizeof(int64_t) * (size_t)(col + 1));
         b->colptr = (int64_t *)batch_alloc(b, sizeof(int64_t) * (size_t)(col + count + 1));
@@ -456,6 +479,25 @@ extern "C" spg_status spgemm_batch_create(int32_t count, const spg_csc *A, const
         }
     }
     if (!s) {
+        // the tasks of each class together, instance order kept inside a class
+        std::vector<int> cls(count);
+        for (int i = 0; i < count; i++) {
+            int c = 0;
+            while (c < kBatchClasses - 1 && maxU[i] > (1u << (kBatchClassLogS[c] - 1))) c++;
+            cls[i] = c;
+        }
+        std::vector<BatchTask> sorted;
+        sorted.reserve(htask.size());
+        for (int c = 0; c < kBatchClasses; c++) {
+            b->class_off[c] = (int64_t)sorted.size();
+            for (const BatchTask &t : htask)
+                if (cls[t.inst] == c) sorted.push_back(t);
+        }
+        b->class_off[kBatchClasses] = (int64_t)sorted.size();
+        s = cuda_check(cudaMemcpy(b->tasks, sorted.data(), sizeof(BatchTask) * sorted.size(), cudaMemcpyHostToDevice),
+                       "tasks");
+    }
+    if (!s) {
         int64_t off = 0;
         for (int i = 0; i < count; i++) {
             b->hinst[i].out_base = off;
@@ -469,12 +511,7 @@ extern "C" spg_status spgemm_batch_create(int32_t count, const spg_csc *A, const
             if (!b->out_row || !b->out_val) s = SPG_OUT_OF_MEMORY;
         }
     }
-    if (!s) {
-        const size_t accsz = 8;
-        b->smem = (sizeof(WarpSeg<double>)) * (size_t)b->warps + (accsz + sizeof(int)) * (size_t)b->warps * (1u << kBatchMaxLogS) +
-                  sizeof(int) * 256 * (size_t)b->warps;
-        s = f64 ? batch_capture<double, int>(b) : batch_capture<long long, int>(b);
-    }
+    if (!s) s = f64 ? batch_capture<double, int>(b) : batch_capture<long long, int>(b);
     if (s) {
         std::string keep = last_error_str();
         spgemm_batch_destroy(b);
