@@ -19,11 +19,12 @@ struct CtaBatch {
     int len[kBatch];
     Acc bv[kBatch];
     int wsum[4][33];
-    int nl, nchunk, ns, nshort;
 };
 
-// Exclusive CTA scan of four counters at once; the totals land in tot[0..3].
-__device__ __forceinline__ void cta_scan4(const int v[4], int ex[4], int (*wsum)[33], int *tot) {
+// Exclusive CTA scan of four counters at once; every thread gets the totals in
+// tot[0..3].  One barrier: every warp reads all warp sums and takes its own
+// offsets, so wsum must not be written again before the caller's next barrier.
+__device__ __forceinline__ void cta_scan4(const int v[4], int ex[4], int (*wsum)[33], int tot[4]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int in[4];
 #pragma unroll
@@ -41,23 +42,12 @@ __device__ __forceinline__ void cta_scan4(const int v[4], int ex[4], int (*wsum)
         for (int q = 0; q < 4; q++) wsum[q][wid] = in[q];
     }
     __syncthreads();
-    if (wid == 0) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            int x = lane < nw ? wsum[q][lane] : 0;
-            int xi = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int t = __shfl_up_sync(kFull, xi, o);
-                if (lane >= o) xi += t;
-            }
-            if (lane < nw) wsum[q][lane] = xi - x;
-            if (lane == 31) tot[q] = xi;
-        }
+    for (int q = 0; q < 4; q++) {
+        const int wt = lane < nw ? wsum[q][lane] : 0;
+        ex[q] = __reduce_add_sync(kFull, lane < wid ? wt : 0) + in[q] - v[q];
+        tot[q] = __reduce_add_sync(kFull, wt);
     }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; q++) ex[q] = wsum[q][wid] + in[q] - v[q];
 }
 
 // One thread's B' entry of a batch: its A~ segment and its value.
@@ -103,9 +93,9 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
         const bool is_long = len >= kLongSeg;
         const int v[4] = {is_long ? 1 : 0, is_long ? (len + 31) >> 5 : 0, (!is_long && len > 0) ? 1 : 0,
                           is_long ? 0 : len};
-        int ex[4];
-        cta_scan4(v, ex, sb.wsum, &sb.nl);
-        const int nl = sb.nl, nch = sb.nchunk, ns = sb.ns, nsp = sb.nshort;
+        int ex[4], tot[4];
+        cta_scan4(v, ex, sb.wsum, tot);
+        const int nl = tot[0], nch = tot[1], ns = tot[2], nsp = tot[3];
         if (is_long) {
             sb.start[ex[0]] = st;
             sb.pref[ex[0]] = ex[1];
