@@ -47,9 +47,33 @@ spg_status cuda_check(cudaError_t e, const char *what) {
 
 // --------------------------------------------------------------- workspace
 
+static void *ws_alloc_direct(spg_plan *p, size_t bytes);
+
+// Workspace: requests up to kArenaMax bytes are carved from chunks of
+// kArenaChunk bytes, each one allocator call (through the caller's callbacks
+// these are calls into Python); larger requests get their own allocation.
+// Everything is released by ws_free_all.
+constexpr size_t kArenaMax = 1 << 20, kArenaChunk = 4 << 20;
+
 void *ws_alloc(spg_plan *p, size_t bytes) {
     if (bytes == 0) bytes = 16;
     bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes > kArenaMax) return ws_alloc_direct(p, bytes);
+    if (!p->arena || p->arena_used + bytes > p->arena_size) {
+        p->arena = (char *)ws_alloc_direct(p, kArenaChunk);
+        if (!p->arena) {
+            p->arena_used = p->arena_size = 0;
+            return nullptr;
+        }
+        p->arena_used = 0;
+        p->arena_size = kArenaChunk;
+    }
+    void *ptr = p->arena + p->arena_used;
+    p->arena_used += bytes;
+    return ptr;
+}
+
+static void *ws_alloc_direct(spg_plan *p, size_t bytes) {
     void *ptr = nullptr;
     if (p->opt.alloc) {
         ptr = p->opt.alloc(bytes, p->opt.alloc_ctx, (void *)p->st);
@@ -75,6 +99,8 @@ void ws_free_all(spg_plan *p) {
             cudaFreeAsync(a.p, p->st);
     }
     p->allocs.clear();
+    p->arena = nullptr;
+    p->arena_used = p->arena_size = 0;
 }
 
 int grid_for(int64_t work, int per_block, int max_blocks) {

@@ -68,6 +68,9 @@ struct spg_plan {
     int sm_count = 0;
 
     std::vector<spg::Alloc> allocs;
+    // small workspace buffers are carved from shared chunks (one allocator call per chunk)
+    char *arena = nullptr;
+    size_t arena_used = 0, arena_size = 0;
     int *d_err = nullptr;
     int64_t *d_cnt = nullptr;      // small device counters (see kCnt* in plan.cu)
     int64_t *h_pinned = nullptr;   // pinned host mirror for read-backs
