@@ -684,11 +684,12 @@ static spg_status plan_build(spg_plan *p) {
     // |D~| in total and per block: read the block boundaries of the scan
     std::vector<int64_t> idx(P + 1);
     for (int i = 0; i <= P; i++) idx[i] = (int64_t)i * W;
+    int64_t *hb = p->h_pinned + 64;
     for (int i = 0; i <= P; i++)
-        TRY(cuda_check(cudaMemcpyAsync(p->h_pinned + i, p->rankpre + idx[i], sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+        TRY(cuda_check(cudaMemcpyAsync(hb + i, p->rankpre + idx[i], sizeof(int64_t), cudaMemcpyDeviceToHost, st),
                        "rank readback"));
     TRY(cuda_check(cudaStreamSynchronize(st), "rank readback"));
-    p->dt_base.assign(p->h_pinned, p->h_pinned + P + 1);
+    p->dt_base.assign(hb, hb + P + 1);
     p->ndt = p->dt_base[P];
     if (p->ndt >= INT32_MAX) {
         set_error("sum of |D~_i| (%lld) exceeds int32", (long long)p->ndt);
@@ -933,7 +934,8 @@ extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_
     int dev = 0;
     spg_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
     if (!s) s = cuda_check(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev), "attr");
-    if (!s) s = cuda_check(cudaMallocHost(&p->h_pinned, sizeof(int64_t) * 64), "cudaMallocHost");
+    // slots 0..63: counters and the error word; 64..64+P: the per-block D~ offsets
+    if (!s) s = cuda_check(cudaMallocHost(&p->h_pinned, sizeof(int64_t) * (64 + (size_t)p->P + 1)), "cudaMallocHost");
     for (int i = 0; i < 8 && !s; i++) s = cuda_check(cudaEventCreate(&p->ev[i]), "event");
     for (int i = 0; i < 10 && !s; i++) s = cuda_check(cudaEventCreate(&p->kev[i]), "event");
     if (!s) s = plan_build(p);

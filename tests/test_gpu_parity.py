@@ -26,6 +26,18 @@ def test_random_small(P, b, vals):
     assert_full_parity(C, ref, f"P={P} b={b} {vals}")
 
 
+@pytest.mark.parametrize("P", [63, 64, 100, 257])
+def test_many_blocks(P):
+    """More blocks than the plan's fixed host counters (and, for P = 257, more
+    blocks than columns of B: some blocks are empty)."""
+    rng = np.random.default_rng(P)
+    A = synth.random_sparse(300, 257, 0.03, rng, values="f64")
+    B = synth.random_sparse(257, 203, 0.03, rng, values="f64")
+    ref = oracle.spgemm(A, B)
+    C = run_gpu(A, B, P, 16)
+    assert_full_parity(C, ref, f"P={P}")
+
+
 @pytest.mark.parametrize("ptr,idx", [(torch.int32, torch.int64), (torch.int64, torch.int32), (torch.int64, torch.int64)])
 def test_index_types(ptr, idx):
     rng = np.random.default_rng(7)
