@@ -20,6 +20,13 @@ Functions and the passages they follow:
                        gather, and C_i = A~_i * B_i with B_i's rows remapped to
                        A~_i's columns.
 * ``block_bounds``  -- column block i is [floor(i*n/P), floor((i+1)*n/P)).
+* ``outer_split``   -- Algorithm 3, first step: B redistributed by row blocks,
+                       column (i, j) = the entries of B(:, j) in row block i.
+* ``merge_matrix``  -- Algorithm 3, last step written as a product: S with
+                       S[i*n + j, j] = 1 sums the partial columns of column j.
+* ``outer_volumes`` -- what Algorithm 3 moves between P owners: B entries that
+                       change owner, partial-product nonzeros, and partial
+                       nonzeros computed away from their column's owner.
 """
 from __future__ import annotations
 
@@ -244,3 +251,63 @@ def spgemm_1d(A, B, P: int, b: int, nthreads: int = 0):
          "absum": np.concatenate([p["absum"] for p in parts]) if mode == 0 and parts else None,
          "nrows": A.nrows, "ncols": B.ncols}
     return C, plans
+
+
+def outer_split(B, P: int):
+    """Algorithm 3, "redistribute B so that p_i owns the i-th row block": the
+    k x (P*n) matrix whose column i*n + j holds the entries of B(:, j) with
+    row in [floor(i*k/P), floor((i+1)*k/P)), rows and values unchanged."""
+    k, n = int(B.nrows), int(B.ncols)
+    rb = block_bounds(k, P)
+    cp = np.asarray(B.colptr, dtype=np.int64)
+    rows = np.asarray(B.rowidx, dtype=np.int64)
+    vals = np.asarray(B.vals)
+    col = np.repeat(np.arange(n, dtype=np.int64), np.diff(cp))
+    blk = np.searchsorted(rb, rows, side="right") - 1
+    key = blk * n + col
+    order = np.argsort(key, kind="stable")
+    colptr = np.zeros(P * n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(key, minlength=P * n), out=colptr[1:])
+    return _View(k, P * n, colptr, rows[order], vals[order])
+
+
+def merge_matrix(n: int, P: int, integer: bool = False):
+    """The (P*n) x n matrix S with S[i*n + j, j] = 1: (A * outer_split(B)) * S
+    adds up the P partial columns of every output column (Algorithm 3, "merge
+    results")."""
+    colptr = np.arange(n + 1, dtype=np.int64) * P
+    rows = (np.arange(P, dtype=np.int64)[None, :] * n + np.arange(n, dtype=np.int64)[:, None]).reshape(-1)
+    vals = np.ones(P * n, dtype=np.int64 if integer else np.float64)
+    return _View(P * n, n, colptr, rows, vals)
+
+
+def outer_volumes(A, B, P: int):
+    """Volumes of Algorithm 3 among P owners, process i owning column block i
+    of A, B and C (the distribution of Algorithm 1): ``b_moved`` = entries of
+    B whose row block differs from their column block; ``partial_nnz`` =
+    sum over i of nnz(A(:, K_i) * B(K_i, :)); ``partial_moved`` = the partial
+    nonzeros of column j computed by a process i that is not j's owner.
+    Plain loops over the entries; for small inputs."""
+    k, n = int(B.nrows), int(B.ncols)
+    rb = block_bounds(k, P)
+    cb = block_bounds(n, P)
+    rblock = lambda r: int(np.searchsorted(rb, r, side="right") - 1)
+    cblock = lambda j: int(np.searchsorted(cb, j, side="right") - 1)
+    cp = np.asarray(B.colptr, dtype=np.int64)
+    rows = np.asarray(B.rowidx, dtype=np.int64)
+    b_moved = 0
+    for j in range(n):
+        for e in range(int(cp[j]), int(cp[j + 1])):
+            b_moved += rblock(int(rows[e])) != cblock(j)
+    acp = np.asarray(A.colptr, dtype=np.int64)
+    arow = np.asarray(A.rowidx, dtype=np.int64)
+    partial_nnz = partial_moved = 0
+    for j in range(n):
+        per_block = {}
+        for e in range(int(cp[j]), int(cp[j + 1])):
+            kk = int(rows[e])
+            per_block.setdefault(rblock(kk), set()).update(arow[acp[kk]:acp[kk + 1]].tolist())
+        for i, rset in per_block.items():
+            partial_nnz += len(rset)
+            partial_moved += len(rset) if i != cblock(j) else 0
+    return {"b_moved": b_moved, "partial_nnz": partial_nnz, "partial_moved": partial_moved}

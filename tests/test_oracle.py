@@ -363,3 +363,80 @@ def test_empty_and_degenerate_shapes():
         oracle.spgemm(z(3, 4), z(5, 2))
     C1, plans = oracle.spgemm_1d(z(3, 4), z(4, 5), P=3, b=2)
     assert C1["colptr"].tolist() == [0] * 6 and all(p["dtilde"].size == 0 for p in plans)
+
+
+# ------------------------------------------------- Algorithm 3 (outer product)
+
+@pytest.mark.parametrize("P", [1, 2, 3, 7, 60])
+def test_outer_split_times_merge_matrix_is_B(P):
+    """Summing the row blocks back together gives B: scipy's product of the
+    split matrix and S equals B entry for entry (P = 60 exceeds k's blocks
+    of more than one row, so some blocks are empty)."""
+    rng = np.random.default_rng(P)
+    B = synth.random_sparse(53, 41, 0.12, rng, values="i64")
+    Bs = oracle.outer_split(B, P)
+    S = oracle.merge_matrix(B.ncols, P, integer=True)
+    back = sp.csc_matrix(to_scipy(Bs) @ to_scipy(S))
+    ref = to_scipy(B)
+    assert (back != ref).nnz == 0
+    assert np.array_equal(np.sort(back.indices), np.sort(ref.indices))
+
+
+@pytest.mark.parametrize("P", [1, 4, 5])
+def test_outer_split_columns_hold_their_row_block(P):
+    """Column i*n + j holds exactly the entries of B(:, j) with row in
+    [floor(i*k/P), floor((i+1)*k/P)), in ascending row order."""
+    rng = np.random.default_rng(10 + P)
+    B = synth.random_sparse(37, 29, 0.2, rng, values="f64")
+    Bs = oracle.outer_split(B, P)
+    k, n = B.nrows, B.ncols
+    for i in range(P):
+        lo, hi = (i * k) // P, ((i + 1) * k) // P
+        for j in range(n):
+            s, e = B.colptr[j], B.colptr[j + 1]
+            rows = B.rowidx[s:e]
+            sel = (rows >= lo) & (rows < hi)
+            c = i * n + j
+            got = Bs.rowidx[Bs.colptr[c]:Bs.colptr[c + 1]]
+            assert np.array_equal(got, rows[sel])
+            assert np.array_equal(Bs.vals[Bs.colptr[c]:Bs.colptr[c + 1]], B.vals[s:e][sel])
+
+
+def test_outer_partial_products_are_dense_block_products():
+    """Column (i, j) of A * outer_split(B) equals the dense product
+    A[:, K_i] @ B[K_i, j], and the partial columns add up to A @ B."""
+    rng = np.random.default_rng(3)
+    A = synth.random_sparse(24, 30, 0.2, rng, values="i32")
+    B = synth.random_sparse(30, 17, 0.2, rng, values="i32")
+    P = 4
+    Ad, Bd = to_dense_csc(A).astype(np.int64), to_dense_csc(B).astype(np.int64)
+    Cp = to_dense(oracle.spgemm(A, oracle.outer_split(B, P)))
+    k, n = B.nrows, B.ncols
+    total = np.zeros((A.nrows, n), dtype=np.int64)
+    for i in range(P):
+        lo, hi = (i * k) // P, ((i + 1) * k) // P
+        blk = Ad[:, lo:hi] @ Bd[lo:hi, :]
+        assert np.array_equal(Cp[:, i * n:(i + 1) * n], blk)
+        total += blk
+    assert np.array_equal(total, Ad @ Bd)
+
+
+def test_outer_volumes_brute_force():
+    """The volume counters against direct enumeration with dense matrices."""
+    rng = np.random.default_rng(5)
+    A = synth.random_sparse(20, 25, 0.25, rng, values="f64")
+    B = synth.random_sparse(25, 18, 0.25, rng, values="f64")
+    P = 3
+    v = oracle.outer_volumes(A, B, P)
+    Ad, Bd = to_dense_csc(A) != 0, to_dense_csc(B) != 0
+    k, n = B.nrows, B.ncols
+    rblk = [max(i for i in range(P) if (i * k) // P <= r) for r in range(k)]
+    cblk = [max(i for i in range(P) if (i * n) // P <= j) for j in range(n)]
+    assert v["b_moved"] == sum(1 for r in range(k) for j in range(n) if Bd[r, j] and rblk[r] != cblk[j])
+    pn = pm = 0
+    for i in range(P):
+        lo, hi = (i * k) // P, ((i + 1) * k) // P
+        pat = (Ad[:, lo:hi].astype(int) @ Bd[lo:hi, :].astype(int)) > 0
+        pn += int(pat.sum())
+        pm += int(sum(pat[:, j].sum() for j in range(n) if cblk[j] != i))
+    assert v["partial_nnz"] == pn and v["partial_moved"] == pm
