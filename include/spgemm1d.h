@@ -322,6 +322,40 @@ spg_status spgemm_plan_labels(const spg_plan *plan, float *y);
  */
 spg_status spgemm_count_noalloc(const spg_csc *A, const spg_csc *B, int64_t *nnz_out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Outer-product 1D SpGEMM (the paper's Algorithm 3, used there for the right
+ * multiplication of the Galerkin product): C = sum over the opt->P row blocks
+ * K_i = [floor(i*k/P), floor((i+1)*k/P)) of B of A(:, K_i) * B(K_i, :).
+ * Steps: B is redistributed by row blocks (column i*n + j of the k x P*n
+ * matrix B' holds the entries of B(:, j) in K_i); C' = A * B' by the column
+ * 1D path with P column blocks, block i reading only A(:, K_i); C = C' * S
+ * with S[i*n + j, j] = 1 (the merge of the partial results), again by the
+ * column 1D path.  The result equals A * B (doubles within the usual
+ * rounding bound, integers exactly).
+ * A, B: device CSC as for spgemm_1d_multiply; opt: as for spgemm_1d_multiply
+ * (P = number of row blocks, b = fetch-block width of both products; learned
+ * sizing is ignored).  C: receives int64 column pointers, row ids of A's
+ * idx_type and double or int64 values, allocated through opt->alloc (or
+ * cudaMallocAsync) and owned by the caller.  B', C' and S are released before
+ * the call returns.  stats (host, may be NULL): the volumes a distributed run
+ * with process i owning column block i of A, B and C would move.  Synchronises
+ * the stream.  Errors: SPG_INVALID_ARGUMENT (NULL pointers, A.ncols != B.nrows,
+ * P < 1), SPG_UNSUPPORTED (int32 row ids of A with P * n >= 2^31), and those
+ * of spgemm_1d_multiply.
+ */
+typedef struct {
+    int64_t P;
+    int64_t products;      /* sum_j flops_j of A * B */
+    int64_t nnzB_moved;    /* entries of B whose row block differs from their column block */
+    int64_t partial_nnz;   /* nnz(C'): the nonzeros of the P partial products together */
+    int64_t partial_moved; /* partial nonzeros of column j computed by a block other than j's owner */
+    int64_t nnzC;
+    double ms_split, ms_local, ms_merge; /* device time of the three steps (CUDA events) */
+} spg_outer_stats;
+
+spg_status spgemm_outer_multiply(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C,
+                                 spg_outer_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

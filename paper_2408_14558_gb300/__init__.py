@@ -311,6 +311,35 @@ def spgemm_1d_multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, val
     return DeviceCSC(c.nrows, c.ncols, colptr, rowidx, vals), st
 
 
+class spg_outer_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "P", "products", "nnzB_moved", "partial_nnz", "partial_moved", "nnzC")] + [
+        (name, ctypes.c_double) for name in ("ms_split", "ms_local", "ms_merge")]
+
+
+def spgemm_outer_multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, validate=True, light_max=0,
+                          slab_rows=0):
+    """Outer-product 1D SpGEMM (Algorithm 3): B redistributed by P row blocks,
+    the P partial products by the column 1D path, then their merge.  C's arrays
+    come from torch's allocator.  Returns (C, stats dict)."""
+    lib = load_library()
+    lib.spgemm_outer_multiply.argtypes = [ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc),
+                                          ctypes.POINTER(spg_options), ctypes.POINTER(spg_csc),
+                                          ctypes.POINTER(spg_outer_stats)]
+    lib.spgemm_outer_multiply.restype = ctypes.c_int
+    alloc = _TorchAllocator(A.colptr.device)
+    opts = make_options(P, b, stream, validate, light_max, slab_rows, SPG_SIZING_EXACT, None, 0.0, allocator=alloc)
+    a, bb, c, st = A.as_c(), B.as_c(), spg_csc(), spg_outer_stats()
+    _check(lib.spgemm_outer_multiply(ctypes.byref(a), ctypes.byref(bb), ctypes.byref(opts), ctypes.byref(c),
+                                     ctypes.byref(st)))
+    idx_dt = torch.int64 if c.idx_type == SPG_IDX_I64 else torch.int32
+    val_dt = torch.float64 if c.val_type == SPG_VAL_F64 else torch.int64
+    colptr = alloc.adopt(c.colptr, 0, torch.int64, c.ncols + 1)
+    rowidx = alloc.adopt(c.rowidx, 0, idx_dt, c.nnz)
+    vals = alloc.adopt(c.vals, 0, val_dt, c.nnz)
+    return DeviceCSC(c.nrows, c.ncols, colptr, rowidx, vals), {n: getattr(st, n) for n, _ in spg_outer_stats._fields_}
+
+
 def spgemm_plan_export(plan: Plan, block: int) -> dict:
     """Planning quantities of one column block as CUDA tensors (for tests)."""
     lib = load_library()

@@ -111,7 +111,7 @@ static void free_user(const spg_options *opt, void *ptr, size_t bytes) {
         cudaFreeAsync(ptr, (cudaStream_t)opt->stream);
 }
 
-static void *alloc_user(const spg_options *opt, size_t bytes) {
+void *spg::alloc_user(const spg_options *opt, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (opt->alloc) return opt->alloc(bytes, opt->alloc_ctx, opt->stream);
     void *p = nullptr;

@@ -170,6 +170,8 @@ void set_error(const char *fmt, ...);
 spg_status cuda_check(cudaError_t e, const char *what);
 void *ws_alloc(spg_plan *p, size_t bytes);
 void ws_free_all(spg_plan *p);
+// Memory handed to the caller (C's arrays): through opt->alloc, else cudaMallocAsync.
+void *alloc_user(const spg_options *opt, size_t bytes);
 spg_status read_dev_err(spg_plan *p, const char *phase);
 int grid_for(int64_t work, int per_block, int max_blocks);
 

@@ -49,6 +49,7 @@ int main(void) {
   printf("%zu %zu %zu\\n", sizeof(spg_csc), sizeof(spg_options), sizeof(spg_stats));
   printf("%zu %zu %zu %zu\\n", offsetof(spg_csc, colptr), offsetof(spg_options, stream),
          offsetof(spg_options, learned_slack), offsetof(spg_stats, ms_plan));
+  printf("%zu %zu\\n", sizeof(spg_outer_stats), offsetof(spg_outer_stats, ms_split));
   return 0;
 }
 """)
@@ -63,6 +64,8 @@ int main(void) {
     assert sizes[4] == g.spg_options.stream.offset
     assert sizes[5] == g.spg_options.learned_slack.offset
     assert sizes[6] == g.spg_stats.ms_plan.offset
+    assert sizes[7] == ctypes.sizeof(g.spg_outer_stats)
+    assert sizes[8] == g.spg_outer_stats.ms_split.offset
 
 
 def test_default_options(lib):
@@ -89,3 +92,22 @@ def test_argument_errors_need_no_gpu(lib):
     B.val_type = g.SPG_VAL_I64
     assert lib.spgemm_plan(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(h)) == g.SPG_INVALID_ARGUMENT
     assert not h.value
+
+
+def test_outer_multiply_argument_errors_need_no_gpu(lib):
+    """spgemm_outer_multiply rejects bad arguments before any CUDA call."""
+    import paper_2408_14558_gb300 as g
+    A = g.spg_csc(4, 5, 0, 0, 0, 0, 0, 1, None, None)
+    B = g.spg_csc(6, 3, 0, 0, 0, 0, 0, 1, None, None)      # 5 != 6
+    o = g.spg_options()
+    lib.spgemm_default_options(ctypes.byref(o))
+    C = g.spg_csc()
+    f = lib.spgemm_outer_multiply
+    f.argtypes = [ctypes.POINTER(g.spg_csc), ctypes.POINTER(g.spg_csc), ctypes.POINTER(g.spg_options),
+                  ctypes.POINTER(g.spg_csc), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    assert f(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(C), None) == g.SPG_INVALID_ARGUMENT
+    B.nrows = 5
+    o.P = 0
+    assert f(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(C), None) == g.SPG_INVALID_ARGUMENT
+    assert f(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), None, None) == g.SPG_INVALID_ARGUMENT
