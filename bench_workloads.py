@@ -202,13 +202,63 @@ def run_batched(args, torch, g, synth):
                 batch_create_ms=create_ms, generation_s=gen_s))
 
 
+def run_galerkin_right(args, torch, g, synth):
+    """The right Galerkin multiplication (R^T A) R (7-point 128^3, 2x2x2
+    aggregation R, P = 32, b = 2048) by the column 1D path (Algorithm 1) and
+    by the outer-product 1D path (Algorithm 3), in the lexicographic ordering
+    and after a random symmetric permutation of the fine grid (the same coarse
+    operator), with the volumes each would move between 32 owners."""
+    N, P, b = 128, 32, 2048
+    A, R, RT = synth.poisson3d(N), synth.aggregation_2x2x2(N), synth.aggregation_2x2x2_transpose(N)
+    timed = _timer(torch)
+    out = {}
+    for order in ("lexicographic", "permuted"):
+        if order == "permuted":
+            q = synth.random_permutation(A.ncols, seed=1)
+            Ao, Ro, RTo = synth.relabel(A, q, q), synth.relabel(R, row_perm=q), synth.relabel(RT, col_perm=q)
+        else:
+            Ao, Ro, RTo = A, R, RT
+        dA, dR, dRT = (g.to_device(M, ptr_dtype=torch.int32, idx_dtype=torch.int32) for M in (Ao, Ro, RTo))
+        RtA, _ = g.spgemm_1d_multiply(dRT, dA, P, b)
+        torch.cuda.synchronize()
+
+        def col():
+            C, _ = g.spgemm_1d_multiply(RtA, dR, P, b)
+            return g.spgemm_last_multiply_stats(), int(C.colptr[-1])
+
+        def outer():
+            C, st = g.spgemm_outer_multiply(RtA, dR, P, b)
+            return st, int(C.colptr[-1])
+        rc = timed(col, max(args.steps, 5), max(args.warmup, 3))
+        ro = timed(outer, max(args.steps, 5), max(args.warmup, 3))
+        ms_c = statistics.median(t for t, _ in rc)
+        ms_o = statistics.median(t for t, _ in ro)
+        sc, nnz_c = rc[0][1]
+        so, nnz_o = ro[0][1]
+        assert nnz_c == nnz_o == 7 * (N // 2) ** 3 - 6 * (N // 2) ** 2
+        out[order] = {"column_1d_ms": ms_c, "outer_1d_ms": ms_o, "products": sc["products"],
+                      "column_1d_gflops": 2 * sc["products"] / (ms_c / 1e3) / 1e9,
+                      "outer_1d_gflops": 2 * so["products"] / (ms_o / 1e3) / 1e9,
+                      "column_1d_fetched_A_entries": sc["gathered_nnz_remote"],
+                      "outer_1d_moved_B_entries": so["nnzB_moved"],
+                      "outer_1d_moved_partial_entries": so["partial_moved"],
+                      "outer_1d_partial_nnz": so["partial_nnz"],
+                      "outer_1d_ms_split_local_merge": [so["ms_split"], so["ms_local"], so["ms_merge"]]}
+    lex = out["lexicographic"]
+    _emit(_base("galerkin_right_RtA_R_128cube_P32_b2048", "(R^T A) R GFLOP/s, column 1D vs outer-product 1D",
+                lex["outer_1d_gflops"], lex["outer_1d_ms"], max(args.steps, 5), max(args.warmup, 3), "f64",
+                {"nnzC": 7 * (N // 2) ** 3 - 6 * (N // 2) ** 2}, orderings=out,
+                note="value = outer-product path, lexicographic ordering; moved/fetched entries are what a "
+                     "32-owner distributed run would transfer"))
+
+
 def run(args):
     import torch
     sys.path.insert(0, ROOT)
     import paper_2408_14558_gb300 as g
     import synth
     g.load_library()
-    fn = {"uniform8192": run_uniform, "galerkin128": run_galerkin, "similarity": run_similarity,
-          "batched": run_batched}[args.workload]
+    fn = {"uniform8192": run_uniform, "galerkin128": run_galerkin, "galerkin_right": run_galerkin_right,
+          "similarity": run_similarity, "batched": run_batched}[args.workload]
     fn(args, torch, g, synth)
     return 0

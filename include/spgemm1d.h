@@ -121,6 +121,8 @@ typedef struct {
     /* device time of kernel groups (CUDA events on the plan's stream):
      * gather = A~ copy; sym/num light = all warp-hash bins; sym/num heavy = dense slabs */
     double ms_gather, ms_sym_light, ms_sym_heavy, ms_num_light, ms_num_heavy;
+    int64_t gathered_nnz_remote; /* of gathered_nnz_exact, the entries whose column lies outside the block's own
+                                    column block of A (what a distributed run fetches from other owners) */
 } spg_stats;
 
 typedef struct spg_plan spg_plan;
@@ -326,11 +328,11 @@ spg_status spgemm_count_noalloc(const spg_csc *A, const spg_csc *B, int64_t *nnz
  * Outer-product 1D SpGEMM (the paper's Algorithm 3, used there for the right
  * multiplication of the Galerkin product): C = sum over the opt->P row blocks
  * K_i = [floor(i*k/P), floor((i+1)*k/P)) of B of A(:, K_i) * B(K_i, :).
- * Steps: B is redistributed by row blocks (column i*n + j of the k x P*n
- * matrix B' holds the entries of B(:, j) in K_i); C' = A * B' by the column
- * 1D path with P column blocks, block i reading only A(:, K_i); C = C' * S
- * with S[i*n + j, j] = 1 (the merge of the partial results), again by the
- * column 1D path.  The result equals A * B (doubles within the usual
+ * Steps: B is redistributed by row blocks (B' holds, for every non-empty
+ * pair (i, j) in (i, j) order, the entries of B(:, j) in K_i); C' = A * B' by
+ * the column 1D path with P column blocks, the columns of row block i reading
+ * only A(:, K_i); C = C' * S with S[c, j(c)] = 1 (the merge of the partial
+ * results), again by the column 1D path.  The result equals A * B (doubles within the usual
  * rounding bound, integers exactly).
  * A, B: device CSC as for spgemm_1d_multiply; opt: as for spgemm_1d_multiply
  * (P = number of row blocks, b = fetch-block width of both products; learned
@@ -340,8 +342,8 @@ spg_status spgemm_count_noalloc(const spg_csc *A, const spg_csc *B, int64_t *nnz
  * the call returns.  stats (host, may be NULL): the volumes a distributed run
  * with process i owning column block i of A, B and C would move.  Synchronises
  * the stream.  Errors: SPG_INVALID_ARGUMENT (NULL pointers, A.ncols != B.nrows,
- * P < 1), SPG_UNSUPPORTED (int32 row ids of A with P * n >= 2^31), and those
- * of spgemm_1d_multiply.
+ * P < 1), SPG_UNSUPPORTED (int32 row ids of A with 2^31 or more non-empty
+ * (i, j) pairs), and those of spgemm_1d_multiply.
  */
 typedef struct {
     int64_t P;

@@ -67,7 +67,8 @@ class spg_stats(ctypes.Structure):
         "light_columns", "heavy_columns", "heavy_items", "empty_columns", "recomputed_columns",
         "nnzB_heavy", "nnzC_heavy", "kernel_launches", "learned_capacity")] + [
         (name, ctypes.c_double) for name in ("ms_plan", "ms_symbolic", "ms_numeric", "ms_gather", "ms_sym_light",
-                                             "ms_sym_heavy", "ms_num_light", "ms_num_heavy")]
+                                             "ms_sym_heavy", "ms_num_light", "ms_num_heavy")] + [
+        ("gathered_nnz_remote", ctypes.c_int64)]
 
 
 _lib = None

@@ -4,13 +4,14 @@
 //                   holds the entries of B(:, j) whose row lies in row block
 //                   i = [floor(i*k/P), floor((i+1)*k/P))  (k_outer_count, a
 //                   scan, k_outer_copy)
+//                   B' keeps only its non-empty columns (most (i, j) pairs
+//                   are empty), in (i, j) order, with the map back to j
 //   local products  C' = A * B' by the column 1D path with P column blocks;
-//                   block i holds the columns i*n .. i*n + n - 1, whose rows
-//                   all lie in K_i, so its owner needs only A(:, K_i): the
-//                   columns it holds (no fetch of A)
-//   merge           C = C' * S with S[i*n + j, j] = 1 (k_outer_merge_matrix):
-//                   the P partial columns of every column added up, by the
-//                   same column 1D path
+//                   the columns of block i have all their rows in K_i, so
+//                   its owner needs only A(:, K_i): the columns it holds
+//   merge           C = C' * S with S[c, j(c)] = 1 (k_outer_merge_fill): the
+//                   partial columns of every column added up, by the same
+//                   column 1D path
 // Volumes of a distributed run (process i owning column block i of A, B and C,
 // as in Algorithm 1) are counted on the way: B entries that change owner in
 // the redistribution and partial nonzeros computed away from their column's
@@ -85,18 +86,53 @@ __global__ void k_outer_copy(const void *Bcp, int p64, const void *Brow, int i64
     }
 }
 
-// S = the (P*n) x n merge matrix: column j holds rows i*n + j, i = 0..P-1,
-// each with value one (double or int64).
-__global__ void k_outer_merge_matrix(int64_t n, int P, int64_t *colptr, void *rows, int i64, void *vals, int f64) {
-    const int64_t tot = n * (int64_t)P;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= tot; t += (int64_t)gridDim.x * blockDim.x) {
-        if (t % P == 0) colptr[t / P] = t;
-        if (t == tot) break;
-        const int64_t j = t / P, i = t % P, r = i * n + j;
+// Flags of the non-empty (i, j) columns, for the scan that numbers them.
+__global__ void k_outer_flags(const unsigned long long *counts, int64_t tot, int64_t *flags) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (int64_t)gridDim.x * blockDim.x)
+        flags[c] = counts[c] > 0;
+}
+
+// The non-empty columns c = i*n + j of B', numbered cid[c]: their column
+// pointers (cp2, nc + 1 entries) and their output column j and row block i.
+__global__ void k_outer_compact(const unsigned long long *counts, const int64_t *cp, const int64_t *cid,
+                                int64_t n, int64_t tot, int64_t *cp2, int32_t *jmap, int32_t *imap) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= tot; c += (int64_t)gridDim.x * blockDim.x) {
+        if (c == tot) {
+            cp2[cid[tot]] = cp[tot];
+        } else if (counts[c]) {
+            const int64_t d = cid[c];
+            cp2[d] = cp[c];
+            jmap[d] = (int32_t)(c % n);
+            imap[d] = (int32_t)(c / n);
+        }
+    }
+}
+
+// Entries per column of the merge matrix: the non-empty blocks of column j.
+__global__ void k_outer_merge_count(const unsigned long long *counts, int64_t n, int P, int64_t *cnt) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = 0;
+        for (int i = 0; i < P; i++) c += counts[(int64_t)i * n + j] > 0;
+        cnt[j] = c;
+    }
+}
+
+// The merge matrix S (nc x n): column j holds the numbers d of the non-empty
+// partial columns of j (ascending, as their blocks ascend), each with value
+// one (double or int64).
+__global__ void k_outer_merge_fill(const unsigned long long *counts, const int32_t *jmap, const int32_t *imap,
+                                   int64_t nc, int64_t n, const int64_t *Scp, void *rows, int i64, void *vals,
+                                   int f64) {
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < nc; d += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = jmap[d];
+        const int i = imap[d];
+        int64_t rank = 0;
+        for (int q = 0; q < i; q++) rank += counts[(int64_t)q * n + j] > 0;
+        const int64_t t = Scp[j] + rank;
         if (i64)
-            ((int64_t *)rows)[t] = r;
+            ((int64_t *)rows)[t] = d;
         else
-            ((int32_t *)rows)[t] = (int32_t)r;
+            ((int32_t *)rows)[t] = (int32_t)d;
         if (f64)
             ((double *)vals)[t] = 1.0;
         else
@@ -105,13 +141,11 @@ __global__ void k_outer_merge_matrix(int64_t n, int P, int64_t *colptr, void *ro
 }
 
 // Partial nonzeros of column j computed by block i != owner(j).
-__global__ void k_outer_partial_moved(const int64_t *__restrict__ Cpcp, int64_t n, int P, unsigned long long *moved) {
+__global__ void k_outer_partial_moved(const int64_t *__restrict__ Cpcp, const int32_t *jmap, const int32_t *imap,
+                                      int64_t nc, int64_t n, int P, unsigned long long *moved) {
     unsigned long long mv = 0;
-    const int64_t tot = n * (int64_t)P;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < tot; c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = c / n, j = c % n;
-        if (i != outer_block(j, n, P)) mv += (unsigned long long)(Cpcp[c + 1] - Cpcp[c]);
-    }
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < nc; d += (int64_t)gridDim.x * blockDim.x)
+        if (imap[d] != outer_block(jmap[d], n, P)) mv += (unsigned long long)(Cpcp[d + 1] - Cpcp[d]);
     mv = warp_sum_ll((long long)mv);
     if ((threadIdx.x & 31) == 0 && mv) atomicAdd(moved, mv);
 }
@@ -153,10 +187,6 @@ extern "C" spg_status spgemm_outer_multiply(const spg_csc *A, const spg_csc *B, 
     const int P = opt->P;
     const int64_t k = B->nrows, n = B->ncols, Pn = (int64_t)P * n;
     const bool a_idx64 = A->idx_type == SPG_IDX_I64;
-    if (!a_idx64 && Pn >= INT32_MAX) {
-        set_error("P * n = %lld partial columns need int64 row ids in A", (long long)Pn);
-        return SPG_UNSUPPORTED;
-    }
     cudaStream_t st = (cudaStream_t)opt->stream;
     spg_outer_stats S{};
     S.P = P;
@@ -175,38 +205,64 @@ extern "C" spg_status spgemm_outer_multiply(const spg_csc *A, const spg_csc *B, 
     spg_status s = SPG_OK;
     spg_csc Bs{}, Cp{}, M{};
     const size_t bib = csc_idx_bytes(*B), bvb = csc_val_bytes(*B);
+    const int p64 = B->ptr_type == SPG_IDX_I64, i64 = B->idx_type == SPG_IDX_I64;
+    const int sm = w.sm_count;
     // --- redistribution of B by row blocks
     unsigned long long *counts = (unsigned long long *)ws_alloc(&w, sizeof(unsigned long long) * (size_t)(Pn + 1));
     unsigned long long *moved = (unsigned long long *)ws_alloc(&w, sizeof(unsigned long long) * 2);
-    if (!counts || !moved) s = SPG_OUT_OF_MEMORY;
+    int64_t *cp = (int64_t *)ws_alloc(&w, sizeof(int64_t) * (size_t)(Pn + 1));
+    int64_t *flags = (int64_t *)ws_alloc(&w, sizeof(int64_t) * (size_t)(Pn + 1));
+    int64_t *cid = (int64_t *)ws_alloc(&w, sizeof(int64_t) * (size_t)(Pn + 1));
+    int64_t *hnc = nullptr;
+    if (!counts || !moved || !cp || !flags || !cid) s = SPG_OUT_OF_MEMORY;
+    if (!s) s = cuda_check(cudaMallocHost(&hnc, sizeof(int64_t)), "cudaMallocHost");
     if (!s) s = cuda_check(cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * (size_t)(Pn + 1), st), "memset");
     if (!s) s = cuda_check(cudaMemsetAsync(moved, 0, sizeof(unsigned long long) * 2, st), "memset");
-    const int p64 = B->ptr_type == SPG_IDX_I64, i64 = B->idx_type == SPG_IDX_I64;
     if (!s && n > 0) {
-        launch(&w, k_outer_count, grid_for(n * 32, 256, w.sm_count * 16), 256, 0, B->colptr, p64, B->rowidx, i64, n,
-               k, P, counts, moved);
+        launch(&w, k_outer_count, grid_for(n * 32, 256, sm * 16), 256, 0, B->colptr, p64, B->rowidx, i64, n, k, P,
+               counts, moved);
         s = cuda_check(cudaGetLastError(), "outer count");
     }
+    if (!s) s = scan_exclusive_i64(&w, (const int64_t *)counts, cp, Pn);
+    if (!s && Pn > 0) {
+        launch(&w, k_outer_flags, grid_for(Pn, 256, sm * 8), 256, 0, counts, Pn, flags);
+        s = cuda_check(cudaGetLastError(), "outer flags");
+    }
+    if (!s) s = scan_exclusive_i64(&w, flags, cid, Pn);
+    if (!s) s = cuda_check(cudaMemcpyAsync(hnc, cid + Pn, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "nc");
+    if (!s) s = cuda_check(cudaStreamSynchronize(st), "nc");
+    const int64_t nc = s ? 0 : *hnc;
+    if (!s && !a_idx64 && nc >= INT32_MAX) {
+        set_error("%lld non-empty partial columns need int64 row ids in A", (long long)nc);
+        s = SPG_UNSUPPORTED;
+    }
+    int32_t *jmap = nullptr, *imap = nullptr;
     if (!s) {
+        jmap = (int32_t *)ws_alloc(&w, sizeof(int32_t) * (size_t)(nc + 1));
+        imap = (int32_t *)ws_alloc(&w, sizeof(int32_t) * (size_t)(nc + 1));
         Bs.nrows = k;
-        Bs.ncols = Pn;
+        Bs.ncols = nc;
         Bs.nnz = B->nnz;
         Bs.ptr_type = SPG_IDX_I64;
         Bs.idx_type = B->idx_type;
         Bs.val_type = B->val_type;
-        Bs.colptr = alloc_user(opt, sizeof(int64_t) * (size_t)(Pn + 1));
+        Bs.colptr = alloc_user(opt, sizeof(int64_t) * (size_t)(nc + 1));
         Bs.rowidx = alloc_user(opt, bib * (size_t)std::max<int64_t>(B->nnz, 1));
         Bs.vals = alloc_user(opt, bvb * (size_t)std::max<int64_t>(B->nnz, 1));
-        if (!Bs.colptr || !Bs.rowidx || !Bs.vals) s = SPG_OUT_OF_MEMORY;
+        if (!jmap || !imap || !Bs.colptr || !Bs.rowidx || !Bs.vals) s = SPG_OUT_OF_MEMORY;
     }
-    if (!s) s = scan_exclusive_i64(&w, (const int64_t *)counts, (int64_t *)Bs.colptr, Pn);
+    if (!s) {
+        launch(&w, k_outer_compact, grid_for(Pn + 1, 256, sm * 8), 256, 0, counts, cp, cid, n, Pn,
+               (int64_t *)Bs.colptr, jmap, imap);
+        s = cuda_check(cudaGetLastError(), "outer compact");
+    }
     if (!s && n > 0 && B->nnz > 0) {
-        launch(&w, k_outer_copy, grid_for(n * 32, 256, w.sm_count * 16), 256, 0, B->colptr, p64, B->rowidx, i64,
-               B->vals, (int)bvb, n, k, P, (const int64_t *)Bs.colptr, Bs.rowidx, Bs.vals);
+        launch(&w, k_outer_copy, grid_for(n * 32, 256, sm * 16), 256, 0, B->colptr, p64, B->rowidx, i64, B->vals,
+               (int)bvb, n, k, P, (const int64_t *)cp, Bs.rowidx, Bs.vals);
         s = cuda_check(cudaGetLastError(), "outer copy");
     }
     cudaEventRecord(ev[1], st);
-    // --- local products C' = A * B' (column block i of B' is process i's)
+    // --- local products C' = A * B' (the columns of row block i are process i's)
     if (!s) {
         spg_options o = *opt;
         s = spgemm_1d_multiply(A, &Bs, &o, &Cp);
@@ -219,29 +275,36 @@ extern "C" spg_status spgemm_outer_multiply(const spg_csc *A, const spg_csc *B, 
         }
     }
     free_csc(opt, Bs);
-    if (!s && Pn > 0) {
-        launch(&w, k_outer_partial_moved, grid_for(Pn, 256, w.sm_count * 8), 256, 0, (const int64_t *)Cp.colptr, n,
-               P, moved + 1);
+    if (!s && nc > 0) {
+        launch(&w, k_outer_partial_moved, grid_for(nc, 256, sm * 8), 256, 0, (const int64_t *)Cp.colptr, jmap, imap,
+               nc, n, P, moved + 1);
         s = cuda_check(cudaGetLastError(), "outer moved");
     }
     cudaEventRecord(ev[2], st);
     // --- merge C = C' * S
+    int64_t *scnt = nullptr;
     if (!s) {
-        M.nrows = Pn;
+        M.nrows = nc;
         M.ncols = n;
-        M.nnz = Pn;
+        M.nnz = nc;
         M.ptr_type = SPG_IDX_I64;
         M.idx_type = a_idx64 ? SPG_IDX_I64 : SPG_IDX_I32;
         M.val_type = Cp.val_type;
         M.colptr = alloc_user(opt, sizeof(int64_t) * (size_t)(n + 1));
-        M.rowidx = alloc_user(opt, csc_idx_bytes(M) * (size_t)std::max<int64_t>(Pn, 1));
-        M.vals = alloc_user(opt, 8 * (size_t)std::max<int64_t>(Pn, 1));
-        if (!M.colptr || !M.rowidx || !M.vals) s = SPG_OUT_OF_MEMORY;
+        M.rowidx = alloc_user(opt, csc_idx_bytes(M) * (size_t)std::max<int64_t>(nc, 1));
+        M.vals = alloc_user(opt, 8 * (size_t)std::max<int64_t>(nc, 1));
+        scnt = (int64_t *)ws_alloc(&w, sizeof(int64_t) * (size_t)(n + 1));
+        if (!M.colptr || !M.rowidx || !M.vals || !scnt) s = SPG_OUT_OF_MEMORY;
     }
-    if (!s) {
-        launch(&w, k_outer_merge_matrix, grid_for(Pn + 1, 256, w.sm_count * 8), 256, 0, n, P, (int64_t *)M.colptr,
-               M.rowidx, (int)a_idx64, M.vals, (int)(M.val_type == SPG_VAL_F64));
-        s = cuda_check(cudaGetLastError(), "merge matrix");
+    if (!s && n > 0) {
+        launch(&w, k_outer_merge_count, grid_for(n, 256, sm * 8), 256, 0, counts, n, P, scnt);
+        s = cuda_check(cudaGetLastError(), "merge count");
+    }
+    if (!s) s = scan_exclusive_i64(&w, scnt, (int64_t *)M.colptr, n);
+    if (!s && nc > 0) {
+        launch(&w, k_outer_merge_fill, grid_for(nc, 256, sm * 8), 256, 0, counts, jmap, imap, nc, n,
+               (const int64_t *)M.colptr, M.rowidx, (int)a_idx64, M.vals, (int)(M.val_type == SPG_VAL_F64));
+        s = cuda_check(cudaGetLastError(), "merge fill");
     }
     if (!s) {
         spg_options o = *opt;
@@ -270,6 +333,7 @@ extern "C" spg_status spgemm_outer_multiply(const spg_csc *A, const spg_csc *B, 
     free_csc(opt, Cp);
     free_csc(opt, M);
     ws_free_all(&w);
+    if (hnc) cudaFreeHost(hnc);
     for (auto &e : ev) cudaEventDestroy(e);
     if (s) set_error("%s", keep.c_str());
     return s;

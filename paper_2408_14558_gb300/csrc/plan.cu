@@ -148,6 +148,7 @@ enum {
     kCntBin0 = 8,  // kNumBins histogram counters
     kCntHeavyItems = 16,
     kCntNnzBHeavy = 17,
+    kCntRemote = 21,
     kCntSlots = 24
 };
 
@@ -269,19 +270,37 @@ __global__ void k_fetch(const uint32_t *H, const uint32_t *D, const int64_t *ran
     }
 }
 
+// Length of every A~ column, the longest, and the entries whose column lies
+// outside the block's own column range [floor(i*k/P), floor((i+1)*k/P)) of A
+// (what a distributed run fetches from other owners); dt_base (P + 1) gives
+// each block's range of D~ entries.
 __global__ void k_gather_len(const int32_t *dtilde, int64_t ndt, const void *Acolptr, int p64,
-                             int64_t *len, long long *maxlen) {
-    long long mx = 0;
+                             int64_t *len, long long *maxlen, const int64_t *dt_base, int P, int64_t k,
+                             long long *remote) {
+    long long mx = 0, rem = 0;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ndt;
          g += (int64_t)gridDim.x * blockDim.x) {
         int64_t h = dtilde[g];
         int64_t l = ld_ptr(Acolptr, p64, h + 1) - ld_ptr(Acolptr, p64, h);
         len[g] = l;
         mx = max(mx, (long long)l);
+        int lo = 0, hi = P;  // the block i with dt_base[i] <= g < dt_base[i + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (dt_base[mid] <= g)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        if (h < (int64_t)lo * k / P || h >= (int64_t)(lo + 1) * k / P) rem += l;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+        rem += __shfl_xor_sync(kFull, rem, o);
+    }
     if ((threadIdx.x & 31) == 0 && mx) atomicMax((unsigned long long *)maxlen, (unsigned long long)mx);
+    if ((threadIdx.x & 31) == 0 && rem) atomicAdd((unsigned long long *)remote, (unsigned long long)rem);
 }
 
 template <typename Acc>
@@ -698,7 +717,10 @@ static spg_status plan_build(spg_plan *p) {
     p->dtilde = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->ndt + 1));
     p->At_colptr = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->ndt + 1));
     int64_t *glen = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->ndt + 1));
-    if (!p->dtilde || !p->At_colptr || !glen) return SPG_OUT_OF_MEMORY;
+    int64_t *d_dt_base = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(P + 1));
+    if (!p->dtilde || !p->At_colptr || !glen || !d_dt_base) return SPG_OUT_OF_MEMORY;
+    TRY(cuda_check(cudaMemcpyAsync(d_dt_base, hb, sizeof(int64_t) * (size_t)(P + 1), cudaMemcpyHostToDevice, st),
+                   "block offsets"));
     if (PW > 0) launch(p, k_dtilde, grid_for(PW, 256, sm * 8), 256, 0, p->Hbits, p->Dbits, p->rankpre, W, PW, p->dtilde);
     if (P * p->nfb > 0)
         launch(p, k_fetch, grid_for(P * p->nfb, 256, sm * 8), 256, 0,
@@ -709,7 +731,7 @@ static spg_status plan_build(spg_plan *p) {
     // --- step 3: gather A~
     if (p->ndt > 0)
         launch(p, k_gather_len, grid_for(p->ndt, 256, sm * 8), 256, 0, p->dtilde, p->ndt, A.colptr, p64A, glen,
-                                                                  (long long *)(p->d_cnt + kCntMaxAcol));
+                                                                  (long long *)(p->d_cnt + kCntMaxAcol), d_dt_base, P, k, (long long *)(p->d_cnt + kCntRemote));
     TRY(scan_exclusive_i64(p, glen, p->At_colptr, p->ndt));
     TRY(cuda_check(cudaMemcpyAsync(p->h_pinned, p->At_colptr + p->ndt, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "readback"));
     TRY(cuda_check(cudaMemcpyAsync(p->h_pinned + 1, p->d_cnt + kCntMaxAcol, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "readback"));
@@ -840,6 +862,7 @@ static spg_status plan_build(spg_plan *p) {
     S.light_columns = n - S.empty_columns - S.heavy_columns;
     S.heavy_items = p->nrec;
     S.nnzB_heavy = p->h_pinned[kCntNnzBHeavy];
+    S.gathered_nnz_remote = p->h_pinned[kCntRemote];
     S.nnzC_heavy = -1;
     float ms = 0;
     cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]);

@@ -336,3 +336,24 @@ def random_sparse(m: int, n: int, density: float, rng, values: str = "f64",
     else:
         vals = _draw_values(rng, nnz, values)
     return _csc_from_sorted(m, n, cols, rows, vals, idx_dtype)
+
+
+def random_permutation(n: int, seed: int = 0) -> np.ndarray:
+    """A seeded permutation of range(n) (an input transform for ordering studies)."""
+    return np.random.default_rng(seed).permutation(n).astype(np.int64)
+
+
+def relabel(M: CSC, row_perm=None, col_perm=None) -> CSC:
+    """The matrix whose entry (row_perm[r], col_perm[c]) is M's entry (r, c):
+    rows and columns renamed by the given permutations (None keeps them).
+    Q A Q^T is relabel(A, q, q); Q R is relabel(R, row_perm=q)."""
+    cp = np.asarray(M.colptr, dtype=np.int64)
+    cols = np.repeat(np.arange(M.ncols, dtype=np.int64), np.diff(cp))
+    rows = np.asarray(M.rowidx, dtype=np.int64)
+    if row_perm is not None:
+        rows = np.asarray(row_perm, dtype=np.int64)[rows]
+    if col_perm is not None:
+        cols = np.asarray(col_perm, dtype=np.int64)[cols]
+    order = np.lexsort((rows, cols))
+    out = _csc_from_sorted(M.nrows, M.ncols, cols[order], rows[order], np.asarray(M.vals)[order])
+    return CSC(out.nrows, out.ncols, out.colptr, out.rowidx.astype(np.asarray(M.rowidx).dtype), out.vals)

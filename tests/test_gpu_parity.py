@@ -120,9 +120,14 @@ def test_planning_phases_match_oracle(P, b):
     dA, dB = g.to_device(A, ptr_dtype=torch.int32), g.to_device(B, ptr_dtype=torch.int32)
     plan = g.spgemm_plan(dA, dB, P, b)
     bounds = oracle.block_bounds(B.ncols, P)
+    own = oracle.block_bounds(A.ncols, P)
+    remote = 0
     for i in range(P):
         ex = g.spgemm_plan_export(plan, i)
         pl = oracle.plan_block(A, B, int(bounds[i]), int(bounds[i + 1]), b)
+        dt = pl["dtilde"]
+        away = dt[(dt < own[i]) | (dt >= own[i + 1])]
+        remote += int(np.sum(A.colptr[away + 1] - A.colptr[away]))
         words = ex["H_bits"].cpu().numpy().view(np.uint32)
         H = np.unpackbits(words.view(np.uint8), bitorder="little")[: A.ncols]
         assert np.array_equal(H, pl["H"]), f"H_{i}"
@@ -136,6 +141,7 @@ def test_planning_phases_match_oracle(P, b):
         assert np.array_equal(ex["flops"].cpu().numpy(), f["flops"])
     st = g.spgemm_plan_stats(plan)
     assert st["products"] == int(oracle.features(A, B)["flops"].sum())
+    assert st["gathered_nnz_remote"] == remote
     g.spgemm_plan_destroy(plan)
 
 
