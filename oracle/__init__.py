@@ -20,6 +20,12 @@ Functions and the passages they follow:
                        gather, and C_i = A~_i * B_i with B_i's rows remapped to
                        A~_i's columns.
 * ``block_bounds``  -- column block i is [floor(i*n/P), floor((i+1)*n/P)).
+* ``flop_bounds``   -- a contiguous column split with balanced flops (the
+                       per-column flop count of Section 3.2 as the weight).
+* ``block_volumes`` -- per block: flops, gathered A~ nonzeros, and those of
+                       columns outside the block's own column block of A (the
+                       communication volume of a distributed run; CV/memA of
+                       the Discussion is their mean over nnz(A)).
 * ``outer_split``   -- Algorithm 3, first step: B redistributed by row blocks,
                        column (i, j) = the entries of B(:, j) in row block i.
 * ``merge_matrix``  -- Algorithm 3, last step written as a product: S with
@@ -207,15 +213,17 @@ class _View:
         self.colptr, self.rowidx, self.vals = colptr, rowidx, vals
 
 
-def spgemm_1d(A, B, P: int, b: int, nthreads: int = 0):
+def spgemm_1d(A, B, P: int, b: int, nthreads: int = 0, bounds=None):
     """Algorithm 1 on one host.  For every block i: H_i, D~_i, fetch blocks,
     A~_i = A(:, D~_i), and C_i = A~_i * B_i where row k of B_i addresses column
     map[k] of A~_i (entries of B_i on rows outside D~_i meet an empty column of
-    A and contribute no product).  C is the concatenation of the C_i.
+    A and contribute no product).  C is the concatenation of the C_i.  The
+    column blocks are block_bounds(n, P) unless ``bounds`` (P + 1 ascending
+    column ids from 0 to n) is given.
     Returns (C dict, list of per-block plan dicts)."""
     if A.ncols != B.nrows:
         raise ValueError("inner dimensions differ")
-    bounds = block_bounds(B.ncols, P)
+    bounds = block_bounds(B.ncols, P) if bounds is None else np.asarray(bounds, dtype=np.int64)
     k = int(B.nrows)
     parts, plans = [], []
     Bcp = np.asarray(B.colptr, dtype=np.int64)
@@ -311,3 +319,44 @@ def outer_volumes(A, B, P: int):
             partial_nnz += len(rset)
             partial_moved += len(rset) if i != cblock(j) else 0
     return {"b_moved": b_moved, "partial_nnz": partial_nnz, "partial_moved": partial_moved}
+
+
+def flop_bounds(A, B, P: int) -> np.ndarray:
+    """Contiguous column blocks with balanced flops: bound_0 = 0, bound_P = n,
+    and for 0 < i < P bound_i is the smallest j whose preceding columns hold
+    at least i/P of the total flops F (P * prefix_j >= i * F in integers)."""
+    fl = features(A, B)["flops"].astype(np.int64)
+    n = int(B.ncols)
+    pre = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(fl, out=pre[1:])
+    F = int(pre[-1])
+    out = np.zeros(P + 1, dtype=np.int64)
+    for i in range(1, P):
+        j = 0
+        while j < n and P * int(pre[j]) < i * F:
+            j += 1
+        out[i] = j
+    out[P] = n
+    return out
+
+
+def block_volumes(A, B, bounds, b: int = 1024):
+    """Per column block [bounds[i], bounds[i+1]): flops, the nonzeros of
+    A~_i = A(:, D~_i), and those among them whose column lies outside the
+    block's own column block [floor(i*k/P), floor((i+1)*k/P)) of A."""
+    bounds = np.asarray(bounds, dtype=np.int64)
+    P = bounds.shape[0] - 1
+    own = block_bounds(int(A.ncols), P)
+    acp = np.asarray(A.colptr, dtype=np.int64)
+    flops, gathered, remote = [], [], []
+    for i in range(P):
+        c0, c1 = int(bounds[i]), int(bounds[i + 1])
+        pl = plan_block(A, B, c0, c1, b)
+        dt = pl["dtilde"]
+        ln = acp[dt + 1] - acp[dt]
+        away = (dt < own[i]) | (dt >= own[i + 1])
+        flops.append(int(features(A, B, c0, c1)["flops"].sum()))
+        gathered.append(int(ln.sum()))
+        remote.append(int(ln[away].sum()))
+    return {"flops": np.array(flops, np.int64), "gathered": np.array(gathered, np.int64),
+            "remote": np.array(remote, np.int64)}

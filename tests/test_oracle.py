@@ -440,3 +440,50 @@ def test_outer_volumes_brute_force():
         pn += int(pat.sum())
         pm += int(sum(pat[:, j].sum() for j in range(n) if cblk[j] != i))
     assert v["partial_nnz"] == pn and v["partial_moved"] == pm
+
+
+# ------------------------------------------------ planning diagnostics
+
+@pytest.mark.parametrize("P", [1, 3, 8])
+def test_flop_bounds_balance(P):
+    """The flop-balanced split: contiguous, from 0 to n, and every block holds
+    at most F/P plus one column's flops (greedy bound), checked against flops
+    recounted by brute force over B's entries."""
+    rng = np.random.default_rng(P)
+    A = synth.random_sparse(60, 50, 0.1, rng, values="f64")
+    B = synth.random_sparse(50, 70, 0.1, rng, values="f64")
+    bd = oracle.flop_bounds(A, B, P)
+    assert bd[0] == 0 and bd[-1] == B.ncols and np.all(np.diff(bd) >= 0)
+    acnt = np.diff(A.colptr)
+    fl = np.array([sum(int(acnt[k]) for k in B.rowidx[B.colptr[j]:B.colptr[j + 1]]) for j in range(B.ncols)])
+    F = int(fl.sum())
+    for i in range(P):
+        blk = int(fl[bd[i]:bd[i + 1]].sum())
+        assert blk <= F / P + fl.max() + 1e-9
+        # the boundary is the first column where the running total reaches i/P
+        if 0 < i < P:
+            pre = np.concatenate([[0], np.cumsum(fl)])
+            assert P * pre[bd[i]] >= i * F and (bd[i] == 0 or P * pre[bd[i] - 1] < i * F)
+
+
+def test_block_volumes_and_explicit_bounds():
+    """Per-block volumes against brute force on dense patterns, and the 1D
+    multiply with explicit bounds equals the unpartitioned product."""
+    rng = np.random.default_rng(11)
+    A = synth.random_sparse(40, 36, 0.12, rng, values="small")
+    B = synth.random_sparse(36, 30, 0.12, rng, values="small")
+    bd = np.array([0, 4, 4, 19, 30])
+    v = oracle.block_volumes(A, B, bd, b=5)
+    Ad, Bd = to_dense_csc(A) != 0, to_dense_csc(B) != 0
+    own = oracle.block_bounds(A.ncols, 4)
+    for i in range(4):
+        need = Bd[:, bd[i]:bd[i + 1]].any(axis=1) & Ad.any(axis=0)     # H_i and D
+        cnt = Ad.sum(axis=0)
+        assert v["gathered"][i] == int(cnt[need].sum())
+        ks = np.flatnonzero(need)
+        assert v["remote"][i] == int(sum(cnt[k] for k in ks if not own[i] <= k < own[i + 1]))
+        assert v["flops"][i] == int(sum(cnt[k] for j in range(bd[i], bd[i + 1]) for k in np.flatnonzero(Bd[:, j])))
+    C, _ = oracle.spgemm_1d(A, B, 4, 5, bounds=bd)
+    ref = oracle.spgemm(A, B)
+    assert np.array_equal(C["colptr"], ref["colptr"]) and np.array_equal(C["rowidx"], ref["rowidx"])
+    assert np.array_equal(C["vals"], ref["vals"])
