@@ -63,6 +63,11 @@ typedef enum {
 typedef enum { SPG_IDX_I32 = 0, SPG_IDX_I64 = 1 } spg_index_type;
 typedef enum { SPG_VAL_F64 = 0, SPG_VAL_I32 = 1, SPG_VAL_I64 = 2 } spg_value_type;
 typedef enum { SPG_SIZING_EXACT = 0, SPG_SIZING_LEARNED = 1 } spg_sizing;
+/* How B's columns are cut into the P blocks: uniformly, [floor(i*n/P),
+ * floor((i+1)*n/P)) (Algorithm 1), or contiguously with balanced flops
+ * (Section 3.2 count as the weight: bound_i is the smallest j whose preceding
+ * columns hold at least i/P of all flops). */
+typedef enum { SPG_SPLIT_UNIFORM = 0, SPG_SPLIT_FLOPS = 1 } spg_split;
 
 /* One CSC matrix.  colptr has ncols + 1 entries of ptr_type; rowidx has nnz
  * entries of idx_type; vals has nnz entries of val_type.  All device memory,
@@ -91,7 +96,7 @@ typedef struct {
     int32_t validate;       /* 1: check that A and B are canonical */
     int32_t light_max;      /* largest per-column bound handled by the warp hash bins (power of two, 32..1024; 0 = 1024) */
     int32_t slab_rows;      /* rows per base slab of the heavy bins (power of two, 1024..16384; 0 = 4096) */
-    int32_t reserved;
+    int32_t split;          /* spg_split (0 = uniform) */
     void *stream;           /* cudaStream_t */
     spg_alloc_fn alloc;
     spg_free_fn free;
@@ -177,6 +182,15 @@ spg_status spgemm_plan_stats(const spg_plan *plan, spg_stats *st);
  * (its plan is gone by then; this keeps a copy).  SPG_INVALID_ARGUMENT if
  * there was none. */
 spg_status spgemm_last_multiply_stats(spg_stats *st);
+
+/* Per-block diagnostics of a plan (host arrays, any may be NULL): bounds
+ * (P + 1 column ids of B's blocks), flops (P, Section 3.2 count per block),
+ * gathered (P, nonzeros of A~_i) and remote (P, those of A~_i whose column lies
+ * outside the block's own column block of A: the communication volume of a
+ * distributed run; the Discussion's CV/memA is their mean over nnz(A)).
+ * Synchronises the stream.  SPG_INVALID_ARGUMENT for a NULL plan. */
+spg_status spgemm_plan_blocks(const spg_plan *plan, int64_t *bounds, int64_t *flops, int64_t *gathered,
+                              int64_t *remote);
 
 /* Release the plan and its workspace (stream-ordered).  NULL is a no-op. */
 spg_status spgemm_plan_destroy(spg_plan *plan);

@@ -30,6 +30,7 @@ SPG_CUDA_ERROR, SPG_TIMEOUT, SPG_UNSUPPORTED, SPG_OVERFLOW_RECOMPUTED = 4, 5, 6,
 SPG_IDX_I32, SPG_IDX_I64 = 0, 1
 SPG_VAL_F64, SPG_VAL_I32, SPG_VAL_I64 = 0, 1, 2
 SPG_SIZING_EXACT, SPG_SIZING_LEARNED = 0, 1
+SPG_SPLIT_UNIFORM, SPG_SPLIT_FLOPS = 0, 1
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_INPUT", 3: "OUT_OF_MEMORY",
                 4: "CUDA_ERROR", 5: "TIMEOUT", 6: "UNSUPPORTED", 7: "OVERFLOW_RECOMPUTED"}
 
@@ -54,7 +55,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 class spg_options(ctypes.Structure):
     _fields_ = [("P", ctypes.c_int32), ("sizing", ctypes.c_int32), ("b", ctypes.c_int64),
                 ("validate", ctypes.c_int32), ("light_max", ctypes.c_int32),
-                ("slab_rows", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("slab_rows", ctypes.c_int32), ("split", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p), ("model", ctypes.c_void_p),
                 ("learned_slack", ctypes.c_double)]
@@ -195,12 +196,12 @@ class _TorchAllocator:
 
 
 def make_options(P=1, b=1024, stream=None, validate=True, light_max=0, slab_rows=0, sizing=SPG_SIZING_EXACT,
-                 model=None, learned_slack=0.0, allocator=None) -> spg_options:
+                 model=None, learned_slack=0.0, allocator=None, split=0) -> spg_options:
     lib = load_library()
     o = spg_options()
     lib.spgemm_default_options(ctypes.byref(o))
     o.P, o.b, o.validate = int(P), int(b), 1 if validate else 0
-    o.light_max, o.slab_rows, o.sizing = int(light_max), int(slab_rows), int(sizing)
+    o.light_max, o.slab_rows, o.sizing, o.split = int(light_max), int(slab_rows), int(sizing), int(split)
     if stream is None:
         stream = torch.cuda.current_stream()
     o.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -235,10 +236,11 @@ class Plan:
 
 
 def spgemm_plan(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, validate=True, light_max=0,
-                slab_rows=0) -> Plan:
+                slab_rows=0, split=0) -> Plan:
+    """Steps 1-4 of Algorithm 1; split = SPG_SPLIT_UNIFORM or SPG_SPLIT_FLOPS."""
     lib = load_library()
     alloc = _TorchAllocator(A.colptr.device)
-    opts = make_options(P, b, stream, validate, light_max, slab_rows, allocator=alloc)
+    opts = make_options(P, b, stream, validate, light_max, slab_rows, allocator=alloc, split=split)
     a, bb = A.as_c(), B.as_c()
     h = ctypes.c_void_p()
     _check(lib.spgemm_plan(ctypes.byref(a), ctypes.byref(bb), ctypes.byref(opts), ctypes.byref(h)))
@@ -295,13 +297,13 @@ def spgemm_plan_destroy(plan: Plan):
 
 
 def spgemm_1d_multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, validate=True, light_max=0,
-                       slab_rows=0, sizing=SPG_SIZING_EXACT, model=None, learned_slack=0.0):
+                       slab_rows=0, sizing=SPG_SIZING_EXACT, model=None, learned_slack=0.0, split=0):
     """plan + symbolic + numeric + destroy in one C call; C's arrays come from
     torch's allocator through the callbacks.  Returns (C, status)."""
     lib = load_library()
     alloc = _TorchAllocator(A.colptr.device)
     opts = make_options(P, b, stream, validate, light_max, slab_rows, sizing,
-                        model.handle if model is not None else None, learned_slack, allocator=alloc)
+                        model.handle if model is not None else None, learned_slack, allocator=alloc, split=split)
     a, bb, c = A.as_c(), B.as_c(), spg_csc()
     st = _check(lib.spgemm_1d_multiply(ctypes.byref(a), ctypes.byref(bb), ctypes.byref(opts), ctypes.byref(c)))
     idx_dt = torch.int64 if c.idx_type == SPG_IDX_I64 else torch.int32
@@ -341,6 +343,25 @@ def spgemm_outer_multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, 
     return DeviceCSC(c.nrows, c.ncols, colptr, rowidx, vals), {n: getattr(st, n) for n, _ in spg_outer_stats._fields_}
 
 
+def spgemm_plan_blocks(plan: Plan) -> dict:
+    """Per-block diagnostics: bounds (P + 1), flops, gathered and remote A~
+    nonzeros (P each, numpy int64), and cv_mem_a = mean remote / nnz(A) (the
+    Discussion's CV/memA)."""
+    import numpy as np
+    lib = load_library()
+    P = plan._keep[2].P
+    out = {q: np.zeros(P + (1 if q == "bounds" else 0), dtype=np.int64)
+           for q in ("bounds", "flops", "gathered", "remote")}
+    ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    lib.spgemm_plan_blocks.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 4
+    lib.spgemm_plan_blocks.restype = ctypes.c_int
+    _check(lib.spgemm_plan_blocks(plan.handle, ptr(out["bounds"]), ptr(out["flops"]), ptr(out["gathered"]),
+                                  ptr(out["remote"])))
+    nnz_a = max(int(plan.A.rowidx.numel()), 1)
+    out["cv_mem_a"] = float(out["remote"].mean()) / nnz_a if P else 0.0
+    return out
+
+
 def spgemm_plan_export(plan: Plan, block: int) -> dict:
     """Planning quantities of one column block as CUDA tensors (for tests)."""
     lib = load_library()
@@ -350,7 +371,8 @@ def spgemm_plan_export(plan: Plan, block: int) -> dict:
     b = plan._keep[2].b
     W = (k + 31) // 32
     nfb = (k + b - 1) // b
-    c0, c1 = block * n // P, (block + 1) * n // P
+    bounds = spgemm_plan_blocks(plan)["bounds"]
+    c0, c1 = int(bounds[block]), int(bounds[block + 1])
     H = torch.zeros(max(W, 1), dtype=torch.int32, device=dev)
     nd = ctypes.c_int64()
     _check(lib.spgemm_plan_export(plan.handle, block, H.data_ptr(), None, ctypes.byref(nd), None, None, None,

@@ -1,5 +1,6 @@
 // C ABI entry points that sit on top of the plan: symbolic, numeric, the
 // one-call multiply, statistics and phase inspection.
+#include <algorithm>
 #include <cstring>
 
 #include "spg_internal.cuh"
@@ -209,11 +210,31 @@ extern "C" spg_status spgemm_plan_export(const spg_plan *pc, int32_t block, void
                                            cudaMemcpyDeviceToDevice, st), "export At vals");
     }
     if (!s && flops) {
-        int64_t c0 = (int64_t)block * p->n / p->P, c1 = (int64_t)(block + 1) * p->n / p->P;
+        const int64_t c0 = p->bounds_h[block], c1 = p->bounds_h[block + 1];
         if (c1 > c0)
             s = cuda_check(cudaMemcpyAsync(flops, p->flops + c0, sizeof(int64_t) * (size_t)(c1 - c0),
                                            cudaMemcpyDeviceToDevice, st), "export flops");
     }
     if (!s) s = cuda_check(cudaStreamSynchronize(st), "export");
+    return s;
+}
+
+extern "C" spg_status spgemm_plan_blocks(const spg_plan *pc, int64_t *bounds, int64_t *flops, int64_t *gathered,
+                                         int64_t *remote) {
+    clear_error();
+    if (!pc) {
+        set_error("plan must not be NULL");
+        return SPG_INVALID_ARGUMENT;
+    }
+    spg_plan *p = const_cast<spg_plan *>(pc);
+    const int P = p->P;
+    if (bounds) std::copy(p->bounds_h.begin(), p->bounds_h.end(), bounds);
+    spg_status s = SPG_OK;
+    int64_t *dst[3] = {flops, gathered, remote};
+    for (int q = 0; q < 3 && !s; q++)
+        if (dst[q])
+            s = cuda_check(cudaMemcpyAsync(dst[q], p->blk + (int64_t)q * P, sizeof(int64_t) * (size_t)P,
+                                           cudaMemcpyDeviceToHost, p->st), "block counters");
+    if (!s) s = cuda_check(cudaStreamSynchronize(p->st), "block counters");
     return s;
 }

@@ -189,14 +189,72 @@ __global__ void k_nonempty_bits(const void *colptr, int p64, int64_t k, int64_t 
     }
 }
 
+// Flop-balanced split: flops of every column of B (Section 3.2 count, from
+// A's column lengths), then bound_i = the smallest j with P * pre[j] >= i * F
+// (pre = exclusive prefix of the flops, F = pre[n]), bound_0 = 0, bound_P = n.
+__global__ void k_split_flops(const void *Bcp, int p64B, const void *Brow, int i64B, const void *Acp, int p64A,
+                              int64_t n, int64_t *fl) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n;
+         j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t s = ld_ptr(Bcp, p64B, j), e = ld_ptr(Bcp, p64B, j + 1);
+        long long f = 0;
+        for (int64_t q = s + lane; q < e; q += 32) {
+            const int64_t kk = ld_ptr(Brow, i64B, q);
+            f += ld_ptr(Acp, p64A, kk + 1) - ld_ptr(Acp, p64A, kk);
+        }
+        f = warp_sum_ll(f);
+        if (lane == 0) fl[j] = f;
+    }
+}
+
+__global__ void k_split_bounds(const int64_t *pre, int64_t n, int P, int64_t *bounds) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > P) return;
+    if (i == 0 || i == P) {
+        bounds[i] = i == 0 ? 0 : n;
+        return;
+    }
+    const int64_t F = pre[n];
+    int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]; P * pre[n] >= i * F always holds
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((__int128)P * pre[mid] >= (__int128)i * F)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    bounds[i] = lo;
+}
+
+// Per-block flops of the plan's split (warp-aggregated when a warp's columns
+// share a block).
+__global__ void k_block_flops(const int64_t *flops, int64_t n, int P, const int64_t *bounds, long long *blk_flops) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = base + lane;
+        const bool valid = j < n;
+        const int i = valid ? block_of_b(j, n, P, bounds) : -1;
+        const long long f = valid ? flops[j] : 0;
+        const int i0 = __shfl_sync(kFull, i, 0);
+        if (__all_sync(kFull, !valid || i == i0)) {
+            const long long t = warp_sum_ll(f);
+            if (lane == 0 && t) atomicAdd((unsigned long long *)(blk_flops + i0), (unsigned long long)t);
+        } else if (valid && f) {
+            atomicAdd((unsigned long long *)(blk_flops + i), (unsigned long long)f);
+        }
+    }
+}
+
 // Warp per column j of B: set bit r of H_{block(j)} for every stored row r.
 __global__ void k_mark_H(const void *colptr, int p64, const void *rowidx, int i64, int64_t n, int P,
-                         int64_t W, uint32_t *H) {
+                         int64_t W, uint32_t *H, const int64_t *bounds) {
     int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t j = warp; j < n; j += nwarps) {
-        int i = block_of(j, n, P);
+        int i = block_of_b(j, n, P, bounds);
         uint32_t *Hi = H + (int64_t)i * W;
         int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
         for (int64_t q = s + lane; q < e; q += 32) {
@@ -276,23 +334,42 @@ __global__ void k_fetch(const uint32_t *H, const uint32_t *D, const int64_t *ran
 // each block's range of D~ entries.
 __global__ void k_gather_len(const int32_t *dtilde, int64_t ndt, const void *Acolptr, int p64,
                              int64_t *len, long long *maxlen, const int64_t *dt_base, int P, int64_t k,
-                             long long *remote) {
+                             long long *remote, long long *blk_gathered, long long *blk_remote) {
+    const int lane = threadIdx.x & 31;
     long long mx = 0, rem = 0;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ndt;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        int64_t h = dtilde[g];
-        int64_t l = ld_ptr(Acolptr, p64, h + 1) - ld_ptr(Acolptr, p64, h);
-        len[g] = l;
-        mx = max(mx, (long long)l);
-        int lo = 0, hi = P;  // the block i with dt_base[i] <= g < dt_base[i + 1]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (dt_base[mid] <= g)
-                lo = mid;
-            else
-                hi = mid;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; base < ndt;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = base + lane;
+        const bool valid = g < ndt;
+        long long l = 0, lr = 0;
+        int lo = -1;
+        if (valid) {
+            const int64_t h = dtilde[g];
+            l = ld_ptr(Acolptr, p64, h + 1) - ld_ptr(Acolptr, p64, h);
+            len[g] = l;
+            mx = max(mx, l);
+            lo = 0;
+            int hi = P;  // the block i with dt_base[i] <= g < dt_base[i + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (dt_base[mid] <= g)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            if (h < (int64_t)lo * k / P || h >= (int64_t)(lo + 1) * k / P) lr = l;
+            rem += lr;
         }
-        if (h < (int64_t)lo * k / P || h >= (int64_t)(lo + 1) * k / P) rem += l;
+        // per-block sums, one atomic per warp when its entries share a block
+        const int b0 = __shfl_sync(kFull, lo, 0);
+        if (__all_sync(kFull, !valid || lo == b0)) {
+            const long long tl = warp_sum_ll(l), tr = warp_sum_ll(lr);
+            if (lane == 0 && tl) atomicAdd((unsigned long long *)(blk_gathered + b0), (unsigned long long)tl);
+            if (lane == 0 && tr) atomicAdd((unsigned long long *)(blk_remote + b0), (unsigned long long)tr);
+        } else if (valid) {
+            if (l) atomicAdd((unsigned long long *)(blk_gathered + lo), (unsigned long long)l);
+            if (lr) atomicAdd((unsigned long long *)(blk_remote + lo), (unsigned long long)lr);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -382,12 +459,12 @@ __global__ void k_gather_copy(const int64_t *__restrict__ At_colptr, const int64
 template <typename Acc>
 __global__ void k_remap_B(const void *colptr, int p64, const void *rowidx, int i64, const void *vals,
                           int vt, int64_t n, int P, const uint32_t *H, const uint32_t *D,
-                          const int64_t *rankpre, int64_t W, int32_t *Bq, Acc *Bv) {
+                          const int64_t *rankpre, int64_t W, int32_t *Bq, Acc *Bv, const int64_t *bounds) {
     int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t j = warp; j < n; j += nwarps) {
-        int i = block_of(j, n, P);
+        int i = block_of_b(j, n, P, bounds);
         int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
         for (int64_t q = s + lane; q < e; q += 32) {
             int64_t r = ld_ptr(rowidx, i64, q);
@@ -679,6 +756,29 @@ static spg_status plan_build(spg_plan *p) {
         TRY(read_dev_err(p, "input validation"));
     }
 
+    // --- column blocks: uniform, or contiguous with balanced flops
+    p->blk = (int64_t *)ws_alloc(p, sizeof(int64_t) * 3 * (size_t)P);
+    if (!p->blk) return SPG_OUT_OF_MEMORY;
+    TRY(cuda_check(cudaMemsetAsync(p->blk, 0, sizeof(int64_t) * 3 * (size_t)P, st), "memset"));
+    p->bounds_h.resize(P + 1);
+    for (int i = 0; i <= P; i++) p->bounds_h[i] = (int64_t)i * n / P;
+    if (p->opt.split == SPG_SPLIT_FLOPS && P > 1 && n > 0) {
+        int64_t *fl = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(n + 1));
+        int64_t *pre = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(n + 1));
+        p->bounds_d = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(P + 1));
+        if (!fl || !pre || !p->bounds_d) return SPG_OUT_OF_MEMORY;
+        launch(p, k_split_flops, grid_for(n * 32, 256, sm * 16), 256, 0, B.colptr, p64B, B.rowidx, i64B, A.colptr,
+               p64A, n, fl);
+        TRY(scan_exclusive_i64(p, fl, pre, n));
+        launch(p, k_split_bounds, grid_for(P + 1, 256, sm), 256, 0, pre, n, P, p->bounds_d);
+        LAUNCH_OK("flop split");
+        int64_t *hb = p->h_pinned + 64;
+        TRY(cuda_check(cudaMemcpyAsync(hb, p->bounds_d, sizeof(int64_t) * (size_t)(P + 1), cudaMemcpyDeviceToHost, st),
+                       "split readback"));
+        TRY(cuda_check(cudaStreamSynchronize(st), "split readback"));
+        p->bounds_h.assign(hb, hb + P + 1);
+    }
+
     // --- step 1: D and H_i
     p->W = (k + 31) / 32;
     const int64_t W = p->W;
@@ -691,7 +791,9 @@ static spg_status plan_build(spg_plan *p) {
     if (!p->Dbits || !p->Hbits || !p->rankpre || !popc || !p->fetch) return SPG_OUT_OF_MEMORY;
     TRY(cuda_check(cudaMemsetAsync(p->Hbits, 0, sizeof(uint32_t) * (size_t)(P * W + 1), st), "memset H"));
     if (W > 0) launch(p, k_nonempty_bits, grid_for(W, 256, sm * 8), 256, 0, A.colptr, p64A, k, W, p->Dbits);
-    if (n > 0) launch(p, k_mark_H, grid_for(n * 32, 256, sm * 16), 256, 0, B.colptr, p64B, B.rowidx, i64B, n, P, W, p->Hbits);
+    if (n > 0)
+        launch(p, k_mark_H, grid_for(n * 32, 256, sm * 16), 256, 0, B.colptr, p64B, B.rowidx, i64B, n, P, W, p->Hbits,
+               p->bounds_d);
     LAUNCH_OK("mark H");
 
     // --- step 2: D~_i = H_i & D, its ranks and Algorithm 2
@@ -731,7 +833,8 @@ static spg_status plan_build(spg_plan *p) {
     // --- step 3: gather A~
     if (p->ndt > 0)
         launch(p, k_gather_len, grid_for(p->ndt, 256, sm * 8), 256, 0, p->dtilde, p->ndt, A.colptr, p64A, glen,
-                                                                  (long long *)(p->d_cnt + kCntMaxAcol), d_dt_base, P, k, (long long *)(p->d_cnt + kCntRemote));
+                                                                  (long long *)(p->d_cnt + kCntMaxAcol), d_dt_base, P, k, (long long *)(p->d_cnt + kCntRemote),
+               (long long *)(p->blk + P), (long long *)(p->blk + 2 * P));
     TRY(scan_exclusive_i64(p, glen, p->At_colptr, p->ndt));
     TRY(cuda_check(cudaMemcpyAsync(p->h_pinned, p->At_colptr + p->ndt, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "readback"));
     TRY(cuda_check(cudaMemcpyAsync(p->h_pinned + 1, p->d_cnt + kCntMaxAcol, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "readback"));
@@ -769,10 +872,11 @@ static spg_status plan_build(spg_plan *p) {
         int g = grid_for(n * 32, 256, sm * 16);
         if (p->acc_f64)
             launch(p, k_remap_B<double>, g, 256, 0, B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P, p->Hbits,
-                                                 p->Dbits, p->rankpre, W, p->Bq, (double *)p->Bv);
+                                                 p->Dbits, p->rankpre, W, p->Bq, (double *)p->Bv, p->bounds_d);
         else
             launch(p, k_remap_B<long long>, g, 256, 0, B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P,
-                                                    p->Hbits, p->Dbits, p->rankpre, W, p->Bq, (long long *)p->Bv);
+                                                    p->Hbits, p->Dbits, p->rankpre, W, p->Bq, (long long *)p->Bv,
+                                                    p->bounds_d);
         LAUNCH_OK("remap B");
     }
 
@@ -793,6 +897,7 @@ static spg_status plan_build(spg_plan *p) {
         launch(p, k_col_stats, grid_for(n * 32, 256, sm * 16), 256, 0,
             B.colptr, p64B, n, p->Bq, p->At_colptr, p->At_row, p->light_max, p->flops, p->win_lo, p->win_hi,
             p->nnzb, p->maxa, p->bin_of, (long long *)(p->d_cnt + kCntBin0), (long long *)(p->d_cnt + kCntProducts));
+        launch(p, k_block_flops, grid_for(n, 256, sm * 8), 256, 0, p->flops, n, P, p->bounds_d, (long long *)p->blk);
         LAUNCH_OK("column stats");
         TRY(bin_columns(p, p->bin_of, p->binlist, p->bin_off));
     }
@@ -925,6 +1030,10 @@ extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_
         return SPG_UNSUPPORTED;
     }
     int lm = opt->light_max ? opt->light_max : 1024;
+    if (opt->split != SPG_SPLIT_UNIFORM && opt->split != SPG_SPLIT_FLOPS) {
+        set_error("split must be SPG_SPLIT_UNIFORM or SPG_SPLIT_FLOPS (got %d)", opt->split);
+        return SPG_INVALID_ARGUMENT;
+    }
     int R = opt->slab_rows ? opt->slab_rows : 4096;
     if (lm < 32 || lm > 1024 || (lm & (lm - 1)) || R < 1024 || R > 16384 || (R & (R - 1))) {
         set_error("light_max must be a power of two in [32, 1024] and slab_rows one in [1024, 16384]");

@@ -120,6 +120,9 @@ struct spg_plan {
     bool symbolic_done = false;
     int32_t *nbinlist = nullptr;
     void *num_items = nullptr;  // one header per numeric item (k_num_heavy)
+    int64_t *bounds_d = nullptr;     // column block bounds (P + 1) of a non-uniform split, else null
+    std::vector<int64_t> bounds_h;   // the bounds in effect (P + 1), host
+    int64_t *blk = nullptr;          // per block: flops, gathered A~ nonzeros, of them fetched (3 x P)
     int64_t nbin_off[spg::kNumBins + 1] = {0};
 
     spg_stats stats{};
@@ -201,6 +204,21 @@ __device__ __forceinline__ int64_t ld_ptr(const void *p, int is64, int64_t i) {
 // Column block of output column j: block i holds [floor(i*n/P), floor((i+1)*n/P)).
 __device__ __forceinline__ int block_of(int64_t j, int64_t n, int P) {
     return (int)(((j + 1) * (int64_t)P - 1) / n);
+}
+
+// The same with explicit bounds (P + 1 ascending column ids from 0 to n, empty
+// blocks allowed) when the plan has them: the largest i with bounds[i] <= j.
+__device__ __forceinline__ int block_of_b(int64_t j, int64_t n, int P, const int64_t *bounds) {
+    if (!bounds) return block_of(j, n, P);
+    int lo = 0, hi = P;  // bounds[lo] <= j < bounds[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bounds[mid] <= j)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
 }
 
 template <typename Acc>

@@ -111,3 +111,16 @@ def test_outer_multiply_argument_errors_need_no_gpu(lib):
     o.P = 0
     assert f(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(C), None) == g.SPG_INVALID_ARGUMENT
     assert f(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), None, None) == g.SPG_INVALID_ARGUMENT
+
+
+def test_split_and_block_argument_errors_need_no_gpu(lib):
+    import paper_2408_14558_gb300 as g
+    assert lib.spgemm_plan_blocks(None, None, None, None, None) == g.SPG_INVALID_ARGUMENT
+    A = g.spg_csc(4, 5, 0, 0, 0, 0, 0, 1, None, None)
+    B = g.spg_csc(5, 3, 0, 0, 0, 0, 0, 1, None, None)
+    o = g.spg_options()
+    lib.spgemm_default_options(ctypes.byref(o))
+    o.split = 7
+    h = ctypes.c_void_p()
+    assert lib.spgemm_plan(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(h)) == g.SPG_INVALID_ARGUMENT
+    assert "split" in g.spgemm_last_error()
