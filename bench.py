@@ -53,7 +53,8 @@ def parse_args(argv=None):
     ap.add_argument("--out-dir", default=os.path.join(tempfile.gettempdir(), "spgemm1d_bench"),
                     help="where the clock samples and the tuning cache are written")
     ap.add_argument("--workload", default="rmat18",
-                    choices=["rmat18", "uniform8192", "galerkin128", "galerkin_right", "similarity", "batched"],
+                    choices=["rmat18", "uniform8192", "galerkin128", "galerkin_right", "similarity", "batched",
+                             "structure"],
                     help="rmat18 is the headline; the others measure the remaining configurations")
     ap.add_argument("--rmat-scale", type=int, default=RMAT_SCALE,
                     help="R-MAT scale of the rmat18 workload (smaller scales for profiler captures)")

@@ -252,6 +252,47 @@ def run_galerkin_right(args, torch, g, synth):
                      "32-owner distributed run would transfer"))
 
 
+def run_structure(args, torch, g, synth):
+    """The paper's "structure matters" finding on synthetic inputs: A*A for a
+    banded 7-point operator (128^3) and an R-MAT graph (scale 18), each in its
+    own ordering and after a random symmetric permutation, with uniform and
+    flop-balanced column blocks (P = 16, b = 1024): CV/memA (mean fetched A
+    volume over nnz(A)), block-granular fetch volume, the largest block's flops
+    over the mean, and the multiply's time on this GPU."""
+    P, b = 16, 1024
+    timed = _timer(torch)
+    rows = []
+    for name, A in (("poisson3d_128", synth.poisson3d(128)), ("rmat_s18_ef16", synth.rmat_symmetric(18, 16, seed=0))):
+        q = synth.random_permutation(A.ncols, seed=2)
+        for order, M in (("original", A), ("permuted", synth.relabel(A, q, q))):
+            dM = g.to_device(M, ptr_dtype=torch.int32, idx_dtype=torch.int32)
+            for split_name, split in (("uniform", g.SPG_SPLIT_UNIFORM), ("flops", g.SPG_SPLIT_FLOPS)):
+                def step():
+                    plan = g.spgemm_plan(dM, dM, P, b, split=split)
+                    cp, _ = g.spgemm_symbolic(plan)
+                    C = g.spgemm_numeric(plan, cp)
+                    blk = g.spgemm_plan_blocks(plan)
+                    st = g.spgemm_plan_stats(plan)
+                    g.spgemm_plan_destroy(plan)
+                    return blk, st
+                res = timed(step, max(args.steps, 3), max(args.warmup, 2))
+                ms = statistics.median(t for t, _ in res)
+                blk, st = res[0][1]
+                fl = blk["flops"]
+                rows.append({"matrix": name, "ordering": order, "split": split_name, "ms": ms,
+                             "gflops": 2 * st["products"] / (ms / 1e3) / 1e9, "cv_mem_a": blk["cv_mem_a"],
+                             "fetched_A_entries": int(blk["remote"].sum()),
+                             "fetch_blocks_chosen": st["fetch_blocks_chosen"],
+                             "gathered_block_volume": st["gathered_nnz_block"], "nnzA": int(M.rowidx.size),
+                             "block_flops_max_over_mean": float(fl.max() / max(fl.mean(), 1))})
+    best = max(r["gflops"] for r in rows)
+    _emit(_base("structure_AxA_poisson128_rmat18_P16_b1024", "CV/memA and block balance, original vs permuted "
+                "ordering, uniform vs flop split", best, min(r["ms"] for r in rows), max(args.steps, 3),
+                max(args.warmup, 2), "f64", {"P": P, "b": b}, cases=rows,
+                note="value = best GFLOP/s of the cases; cv_mem_a is what a 16-owner distributed run would fetch "
+                     "per owner over nnz(A)"))
+
+
 def run(args):
     import torch
     sys.path.insert(0, ROOT)
@@ -259,6 +300,6 @@ def run(args):
     import synth
     g.load_library()
     fn = {"uniform8192": run_uniform, "galerkin128": run_galerkin, "galerkin_right": run_galerkin_right,
-          "similarity": run_similarity, "batched": run_batched}[args.workload]
+          "similarity": run_similarity, "batched": run_batched, "structure": run_structure}[args.workload]
     fn(args, torch, g, synth)
     return 0
