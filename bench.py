@@ -330,6 +330,14 @@ def main(argv=None):
     comp = sum(compulsory_bytes(st) for st in stats[0])
     path_gbs = comp / (ms_per_step / 1e3) / 1e9
     launches = sum(st["kernel_launches"] for sts in stats for st in sts)
+    # compute-side roofline of the f64 run's numeric phase: every product is one
+    # DMUL and, inside the shared-memory atomic add of a double, one DADD on the
+    # FP64 pipe, which retires 2 lane-operations per clock per SM
+    f64_num_ms = statistics.mean(sts[0]["ms_numeric"] for sts in stats)
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp64_peak = 2.0 * n_sm * sm_mhz * 1e6 / 1e9                       # G lane-ops/s
+    fp64_achieved = 2.0 * stats[0][0]["products"] / (f64_num_ms / 1e3) / 1e9 if f64_num_ms > 0 else 0.0
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -341,6 +349,10 @@ def main(argv=None):
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
             "path_roofline": {"compulsory_bytes_per_step": comp, "achieved": path_gbs, "frac": path_gbs / peak,
                               "unit": "GB/s"},
+            "compute_roofline": {"bound": "fp64 pipe", "scope": "numeric phase of the f64 run",
+                                 "achieved": fp64_achieved, "peak": fp64_peak, "unit": "G lane-ops/s",
+                                 "frac": fp64_achieved / fp64_peak if fp64_peak else 0.0,
+                                 "peak_source": f"2 FP64 lane-ops per clock per SM x {n_sm} SMs x {sm_mhz:.0f} MHz"},
             "kernel_ms_per_step": {k: round(v, 4) for k, v in per_group.items()},
             "kernel_ms_per_run": {label: {gname: round(statistics.mean(sts[ri]["ms_" + gname] for sts in stats), 4)
                                           for gname in groups + ["plan", "symbolic", "numeric"]}
