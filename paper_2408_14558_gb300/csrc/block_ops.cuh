@@ -45,6 +45,35 @@ __device__ __forceinline__ int cta_scan_popc(const uint32_t *bits, int *pre, int
     return total;
 }
 
+// The same scan with one barrier: pre[] is complete for every thread only
+// after the caller's next barrier, and wsum must not be written again before
+// that barrier.
+__device__ __forceinline__ int cta_scan_popc1(const uint32_t *bits, int *pre, int n, int *wsum) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int per = (n + nt - 1) / nt;
+    const int w0 = tid * per;
+    int local = 0;
+    for (int w = w0; w < min(n, w0 + per); w++) local += __popc(bits[w]);
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    const int wt = lane < nw ? wsum[lane] : 0;
+    const int before = __reduce_add_sync(kFull, lane < wid ? wt : 0);
+    const int total = __reduce_add_sync(kFull, wt);
+    int run = before + incl - local;
+    for (int w = w0; w < min(n, w0 + per); w++) {
+        pre[w] = run;
+        run += __popc(bits[w]);
+    }
+    return total;
+}
+
 // The same scan over packed (word, prefix) pairs: fills bp[w].y and returns
 // the total to every thread.  One barrier: every warp then reads all warp
 // totals and takes its own offset, so the y fields are complete for every

@@ -32,7 +32,10 @@ constexpr int kH = 32, kF = 4;
 constexpr int kW1 = 0, kB1 = kW1 + kH * kF, kW2 = kB1 + kH, kB2 = kW2 + kH * kH, kW3 = kB2 + kH, kB3 = kW3 + kH;
 constexpr int kNP = kB3 + 1;  // 1249
 static_assert(kNP == 1249, "parameter layout");
-constexpr int kFusedRows = 8192;  // rows of one fused heavy item (dense accumulator in shared memory)
+#ifndef SPG_FUSED_ROWS
+#define SPG_FUSED_ROWS 8192
+#endif
+constexpr int kFusedRows = SPG_FUSED_ROWS;  // rows of one fused heavy item (dense accumulator in shared memory)
 
 const char *last_error_str();
 void clear_error();
@@ -297,14 +300,15 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
-// Heavy columns, one pass: CTA per item of <= kFusedRows rows of one column.
-// Every product sets its row bit and adds into a dense row accumulator; the
-// item's count is then exact, its room is reserved inside the column's
-// predicted room (atomically, items of a column land in any order), and the
-// item is written there in row order.  An item that does not fit flags its
-// column (the count still adds to colfill, which ends as the exact nnz).
-// The accumulator is cleared row by row as it is read, so it is zero again
-// for the next item.
+// Heavy columns, one pass: CTA per item of <= kFusedRows rows of one column,
+// items claimed one at a time from a device counter.  Every product sets its
+// row bit and adds into a dense row accumulator; the item's count is then
+// exact, its room is reserved inside the column's predicted room (atomically,
+// items of a column land in any order), and the item is written there in row
+// order, one bitmap word per warp step (the set bits of a word are consecutive
+// entries: coalesced).  An item that does not fit flags its column (the count
+// still adds to colfill, which ends as the exact nnz).  The accumulator is
+// cleared as it is read, so it is zero again for the next item.
 template <typename Acc, typename OutIdx>
 __global__ void __launch_bounds__(kBatch)
     k_fused_heavy(int64_t nitems, const int32_t *__restrict__ it_rec0, const int32_t *__restrict__ it_nrec,
@@ -315,17 +319,18 @@ __global__ void __launch_bounds__(kBatch)
                   const int64_t *__restrict__ capoff, const int64_t *__restrict__ cap,
                   unsigned long long *__restrict__ colfill, int32_t *flag, unsigned long long *nflag,
                   int32_t *__restrict__ item_cnt, int64_t *__restrict__ item_pos, OutIdx *__restrict__ trow,
-                  Acc *__restrict__ tval) {
+                  Acc *__restrict__ tval, unsigned long long *next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaBatch<Acc> &sb = *(CtaBatch<Acc> *)smem_raw;
     Acc *acc = (Acc *)(smem_raw + ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15));
     uint32_t *bits = (uint32_t *)(acc + kFusedRows);
     int *pre = (int *)(bits + kFusedRows / 32);
     __shared__ int wsum[33];
-    __shared__ long long pos_sh;
+    __shared__ long long pos_sh, claim;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = threadIdx.x; i < kFusedRows; i += blockDim.x) acc[i] = Acc(0);
     const int RW = R >> 5;
-    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    for (int64_t it = cta_claim(next, &claim); it < nitems; it = cta_claim(next, &claim)) {
         const int r0 = it_rec0[it], nr = it_nrec[it];
         const int j = rec_col[r0], t0 = rec_slab[r0];
         const int nwords = nr * RW;
@@ -342,8 +347,8 @@ __global__ void __launch_bounds__(kBatch)
             }
         };
         const SegReg<Acc> first = cta_first_seg<Acc>(p0, p1, seg);
+        // (the first barrier of cta_products orders this before every product)
         for (int w = threadIdx.x; w < nwords; w += blockDim.x) bits[w] = 0;
-        __syncthreads();
         cta_products<true, SPG_NUM_UNROLL, Acc>(
             p0, p1, sb, At_row, At_val, first, seg,
             [&](int r, Acc v) {
@@ -351,7 +356,7 @@ __global__ void __launch_bounds__(kBatch)
                 atomicOr(bits + (lr >> 5), 1u << (lr & 31));
                 atomic_add_acc(acc + lr, v);
             });
-        const int cnt = cta_scan_popc(bits, pre, nwords, wsum);
+        const int cnt = cta_scan_popc1(bits, pre, nwords, wsum);
         if (threadIdx.x == 0) {
             long long pos = (long long)atomicAdd(colfill + j, (unsigned long long)cnt);
             if (pos + cnt > cap[j]) {
@@ -365,22 +370,17 @@ __global__ void __launch_bounds__(kBatch)
         __syncthreads();
         const long long pos = pos_sh;
         const int64_t base = pos >= 0 ? capoff[j] + pos : 0;
-        for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
-            uint32_t word = bits[w];
-            int64_t o = base + pre[w];
-            while (word) {
-                const int bb = __ffs(word) - 1;
-                const int lr = w * 32 + bb;
-                if (pos >= 0) {
-                    trow[o] = (OutIdx)(rbase + lr);
-                    tval[o] = acc[lr];
-                    o++;
-                }
-                acc[lr] = Acc(0);
-                word &= word - 1u;
+        for (int w = wid; w < nwords; w += nw) {
+            const uint32_t word = bits[w];
+            if (((word >> lane) & 1u) == 0) continue;
+            const int lr = w * 32 + lane;
+            if (pos >= 0) {
+                const int64_t o = base + pre[w] + __popc(word & ((1u << lane) - 1u));
+                st_stream(trow + o, (OutIdx)(rbase + lr));
+                st_stream(tval + o, acc[lr]);
             }
+            acc[lr] = Acc(0);
         }
-        __syncthreads();
     }
 }
 
@@ -815,6 +815,8 @@ static spg_status learned_kernels(spg_plan *p, LearnedState &L) {
     size_t smem = ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15) + sizeof(Acc) * kFusedRows +
                   sizeof(uint32_t) * (kFusedRows / 32) + sizeof(int) * (kFusedRows / 32 + 1);
     auto kern = k_fused_heavy<Acc, OutIdx>;
+    spg_status s0 = cuda_check(cudaMemsetAsync(p->d_cnt + kCntFusedNextSlot, 0, sizeof(int64_t), p->st), "memset");
+    if (s0) return s0;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBatch, smem);
@@ -822,7 +824,7 @@ static spg_status learned_kernels(spg_plan *p, LearnedState &L) {
     launch(p, kern, grid_for(L.nitems, 1, p->sm_count * occ), kBatch, smem, L.nitems, L.it_rec0, L.it_nrec, p->rec_col,
            p->rec_slab, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv, p->At_colptr, p->At_row,
            (const Acc *)p->At_val, p->split, p->T, p->R, L.capoff, L.cap, L.colfill, L.flag, L.nflag, L.item_cnt,
-           L.item_pos, (OutIdx *)L.trow, (Acc *)L.tval);
+           L.item_pos, (OutIdx *)L.trow, (Acc *)L.tval, (unsigned long long *)(p->d_cnt + kCntFusedNextSlot));
     return cuda_check(cudaGetLastError(), "fused heavy");
 }
 

@@ -151,6 +151,7 @@ constexpr int kCntNnzCHeavySlot = 18;
 // and numeric heavy kernels (CTAs claim items one at a time, in column order).
 constexpr int kCntSymNextSlot = 19;
 constexpr int kCntNumNextSlot = 20;
+constexpr int kCntFusedNextSlot = 22;  // next item of the learned path's fused heavy kernel
 
 // Claim the next item for the whole CTA; every thread must call it, and the
 // CTA must have passed a barrier since the previous claim was read.
