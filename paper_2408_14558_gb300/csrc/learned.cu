@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kBatch)
             p0, p1, sb, At_row, At_val, first, seg,
             [&](int r, Acc v) {
                 const int lr = (int)(r - rbase);
-                atomicOr(bits + (lr >> 5), 1u << (lr & 31));
+                set_bit_shared(bits + (lr >> 5), 1u << (lr & 31));
                 atomic_add_acc(acc + lr, v);
             });
         const int cnt = cta_scan_popc1(bits, pre, nwords, wsum);

@@ -369,6 +369,20 @@ __device__ __forceinline__ T ld_stream(const T *p) {
 #define SPG_EARLY_ROWS 0
 #endif
 
+// Set bit b of a shared bitmap word; with SPG_TEST_FIRST the word is read
+// first and the atomic skipped when the bit is already set (bits are only ever
+// set during a pass, so a stale read can only cause a redundant atomic).
+#ifndef SPG_TEST_FIRST
+#define SPG_TEST_FIRST 1
+#endif
+__device__ __forceinline__ void set_bit_shared(uint32_t *word, uint32_t mask) {
+#if SPG_TEST_FIRST
+    if ((*(volatile uint32_t *)word & mask) == 0) atomicOr(word, mask);
+#else
+    atomicOr(word, mask);
+#endif
+}
+
 // Minimum resident CTAs per SM asked of the compiler for k_num_heavy: four
 // (60 registers a thread) fill the register file and the shared memory of an
 // SM with the default table; more CTAs hide more of the kernel's latency.

@@ -85,7 +85,7 @@ __global__ void SPG_SYM_BOUNDS
         const int wbase = t0 * RW;
         cta_products<false, SPG_SYM_UNROLL, long long>(
             p0, p1, sb, At_row, (const long long *)nullptr, first, seg,
-            [&](int r, long long) { atomicOr(bits + ((r >> 5) - wbase), 1u << (r & 31)); });
+            [&](int r, long long) { set_bit_shared(bits + ((r >> 5) - wbase), 1u << (r & 31)); });
         // cta_products ends with a barrier: the bitmap is complete
         uint32_t *dst = hbits + (int64_t)r0 * RW;
         for (int w = threadIdx.x; w < nwords; w += blockDim.x) st_stream(dst + w, bits[w]);
