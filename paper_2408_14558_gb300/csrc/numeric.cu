@@ -198,13 +198,19 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
             cta_products<true, SPG_NUM_UNROLL, Acc>(
                 h.p0, h.p1, sb, At_row, At_val, first, seg,
                 [&](int r, Acc v) {
-                    // a row missing from the symbolic bitmap (never expected) goes
-                    // to the dump slot acc[cap] and is reported
                     const uint2 x = bp[(r >> 5) - wbase];
                     const uint32_t sh = r & 31;
+#if SPG_CHECK_MEMBERSHIP
+                    // a row missing from the symbolic bitmap (never expected) goes
+                    // to the dump slot acc[cap] and is reported
                     const bool hit = (x.x >> sh) & 1u;
                     miss |= !hit;
                     atomic_add_acc(acc + (hit ? (int)(x.y + __popc(x.x & ((1u << sh) - 1u))) : cap), v);
+#else
+                    // the rank of a present row; an absent one would still land
+                    // inside [0, cnt] (never outside the accumulator)
+                    atomic_add_acc(acc + (int)(x.y + __popc(x.x & ((1u << sh) - 1u))), v);
+#endif
                 });
             if (miss) bad_sh = 1;
             if (tid == 0 && (long long)nxt < nitems) nh = items[nxt];

@@ -383,6 +383,14 @@ __device__ __forceinline__ void set_bit_shared(uint32_t *word, uint32_t mask) {
 #endif
 }
 
+// k_num_heavy checks that every product's row is in the symbolic bitmap (1)
+// or relies on the two passes enumerating the same products (0: they walk the
+// same segments with the same code, and every row lies in exactly one record
+// whose bitmap the item loads; the item's entry count is still checked).
+#ifndef SPG_CHECK_MEMBERSHIP
+#define SPG_CHECK_MEMBERSHIP 0
+#endif
+
 // Minimum resident CTAs per SM asked of the compiler for k_num_heavy: four
 // (60 registers a thread) fill the register file and the shared memory of an
 // SM with the default table; more CTAs hide more of the kernel's latency.
