@@ -58,7 +58,9 @@ __global__ void SPG_SYM_BOUNDS
                 const int32_t *__restrict__ rec_col, const int32_t *__restrict__ rec_slab, const void *Bcolptr,
                 int p64, const int32_t *__restrict__ Bq, const int64_t *__restrict__ At_colptr,
                 const int32_t *__restrict__ At_row, const int32_t *__restrict__ split, int T, int R,
-                uint32_t *__restrict__ hbits, int32_t *__restrict__ rec_cnt, unsigned long long *next) {
+                uint32_t *__restrict__ hbits, int32_t *__restrict__ rec_cnt, unsigned long long *next,
+                const int64_t *__restrict__ flops, const int32_t *__restrict__ win_lo,
+                const int32_t *__restrict__ win_hi) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RW = R >> 5;
     CtaBatch<long long> &sb = *(CtaBatch<long long> *)smem_raw;
@@ -83,9 +85,17 @@ __global__ void SPG_SYM_BOUNDS
         for (int w = threadIdx.x; w < nwords; w += blockDim.x) bits[w] = 0;
         __syncthreads();
         const int wbase = t0 * RW;
+        // many products per row of the column's window: most bits get set
+        // again and again, so read before the atomic
+        const bool dense = flops[j] > 4 * (int64_t)(win_hi[j] - win_lo[j] + 1);
         cta_products<false, SPG_SYM_UNROLL, long long>(
             p0, p1, sb, At_row, (const long long *)nullptr, first, seg,
-            [&](int r, long long) { set_bit_shared(bits + ((r >> 5) - wbase), 1u << (r & 31)); });
+            [&](int r, long long) {
+                if (dense)
+                    set_bit_shared(bits + ((r >> 5) - wbase), 1u << (r & 31));
+                else
+                    atomicOr(bits + ((r >> 5) - wbase), 1u << (r & 31));
+            });
         // cta_products ends with a barrier: the bitmap is complete
         uint32_t *dst = hbits + (int64_t)r0 * RW;
         for (int w = threadIdx.x; w < nwords; w += blockDim.x) st_stream(dst + w, bits[w]);
@@ -184,7 +194,8 @@ static spg_status symbolic_heavy(spg_plan *p) {
     group_begin(p, kKSymHeavy);
     launch(p, k_sym_heavy, g, threads, smem, p->nsym, p->sym_rec0, p->sym_nrec, p->rec_col, p->rec_slab,
            p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr, p->At_row, p->split, p->T, p->R,
-           p->hbits, p->rec_cnt, (unsigned long long *)(p->d_cnt + kCntSymNextSlot));
+           p->hbits, p->rec_cnt, (unsigned long long *)(p->d_cnt + kCntSymNextSlot), p->flops, p->win_lo,
+           p->win_hi);
     group_end(p, kKSymHeavy);
     int64_t *nnum = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
     int64_t *num_first = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
