@@ -164,10 +164,17 @@ __global__ void k_validate(const void *colptr, int p64, const void *rowidx, int 
         int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
         bool bad = (s > e) || (s < 0) || (e > nnz);
         if (!bad) {
-            for (int64_t q = s + lane; q < e; q += 32) {
-                int64_t r = ld_ptr(rowidx, i64, q);
-                if (r < 0 || r >= nrows) bad = true;
-                if (q > s && ld_ptr(rowidx, i64, q - 1) >= r) bad = true;
+            for (int64_t q0 = s + lane; q0 < e; q0 += 32 * 4) {
+                int64_t r[4], pr[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int64_t q = q0 + 32 * u;
+                    r[u] = q < e ? ld_ptr(rowidx, i64, q) : 0;
+                    pr[u] = (q < e && q > s) ? ld_ptr(rowidx, i64, q - 1) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (r[u] < 0 || r[u] >= nrows || pr[u] >= r[u]) bad = true;
             }
         }
         if (__any_sync(kFull, bad) && lane == 0) atomicOr(err, kDevErrInput);
@@ -257,9 +264,13 @@ __global__ void k_mark_H(const void *colptr, int p64, const void *rowidx, int i6
         int i = block_of_b(j, n, P, bounds);
         uint32_t *Hi = H + (int64_t)i * W;
         int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
-        for (int64_t q = s + lane; q < e; q += 32) {
-            int64_t r = ld_ptr(rowidx, i64, q);
-            atomicOr(Hi + (r >> 5), 1u << (r & 31));
+        for (int64_t q0 = s + lane; q0 < e; q0 += 32 * 8) {
+            int64_t r[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) r[u] = q0 + 32 * u < e ? ld_ptr(rowidx, i64, q0 + 32 * u) : -1;
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (r[u] >= 0) atomicOr(Hi + (r[u] >> 5), 1u << (r[u] & 31));
         }
     }
 }
@@ -466,15 +477,28 @@ __global__ void k_remap_B(const void *colptr, int p64, const void *rowidx, int i
     for (int64_t j = warp; j < n; j += nwarps) {
         int i = block_of_b(j, n, P, bounds);
         int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
-        for (int64_t q = s + lane; q < e; q += 32) {
-            int64_t r = ld_ptr(rowidx, i64, q);
-            int64_t w = r >> 5;
-            uint32_t word = H[(int64_t)i * W + w] & D[w];
-            int32_t loc = -1;
-            if ((word >> (r & 31)) & 1u)
-                loc = (int32_t)(rankpre[(int64_t)i * W + w] + __popc(word & ((1u << (r & 31)) - 1u)));
-            Bq[q] = loc;
-            Bv[q] = load_val<Acc>(vals, vt, q);
+        for (int64_t q0 = s + lane; q0 < e; q0 += 32 * 4) {
+            int64_t r[4];
+            uint32_t word[4];
+            int64_t pre[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) r[u] = q0 + 32 * u < e ? ld_ptr(rowidx, i64, q0 + 32 * u) : -1;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t w = r[u] >= 0 ? r[u] >> 5 : 0;
+                word[u] = r[u] >= 0 ? H[(int64_t)i * W + w] & D[w] : 0;
+                pre[u] = r[u] >= 0 ? rankpre[(int64_t)i * W + w] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t q = q0 + 32 * u;
+                if (q >= e) continue;
+                const uint32_t sh = (uint32_t)(r[u] & 31);
+                int32_t loc = -1;
+                if ((word[u] >> sh) & 1u) loc = (int32_t)(pre[u] + __popc(word[u] & ((1u << sh) - 1u)));
+                Bq[q] = loc;
+                Bv[q] = load_val<Acc>(vals, vt, q);
+            }
         }
     }
 }
@@ -511,16 +535,26 @@ __global__ void k_col_stats(const void *Bcolptr, int p64, int64_t n, const int32
         int64_t s = ld_ptr(Bcolptr, p64, j), e = ld_ptr(Bcolptr, p64, j + 1);
         long long fl = 0;
         int mx = 0, lo = INT32_MAX, hi = -1;
-        for (int64_t q = s + lane; q < e; q += 32) {
-            int loc = Bq[q];
-            if (loc >= 0) {
-                int64_t a0 = At_colptr[loc], a1 = At_colptr[loc + 1];
-                int len = (int)(a1 - a0);
+        // four entries per lane and step, each stage's loads issued together
+        // (long columns of B would otherwise be a chain of dependent loads)
+        for (int64_t q0 = s + lane; q0 < e; q0 += 32 * 4) {
+            int loc[4];
+            int64_t a0[4], a1[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) loc[u] = q0 + 32 * u < e ? Bq[q0 + 32 * u] : -1;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                a0[u] = loc[u] >= 0 ? At_colptr[loc[u]] : 0;
+                a1[u] = loc[u] >= 0 ? At_colptr[loc[u] + 1] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int len = (int)(a1[u] - a0[u]);
                 fl += len;
                 mx = max(mx, len);
                 if (len > 0) {
-                    lo = min(lo, At_row[a0]);
-                    hi = max(hi, At_row[a1 - 1]);
+                    lo = min(lo, At_row[a0[u]]);
+                    hi = max(hi, At_row[a1[u] - 1]);
                 }
             }
         }
