@@ -487,3 +487,62 @@ def test_block_volumes_and_explicit_bounds():
     ref = oracle.spgemm(A, B)
     assert np.array_equal(C["colptr"], ref["colptr"]) and np.array_equal(C["rowidx"], ref["rowidx"])
     assert np.array_equal(C["vals"], ref["vals"])
+
+
+# ------------------------------------------------ betweenness centrality
+
+def _undirected(n, edges):
+    rows, cols = [], []
+    for a, b in edges:
+        rows += [a, b]
+        cols += [b, a]
+    order = np.lexsort((rows, cols))
+    return synth._csc_from_sorted(n, n, np.array(cols)[order], np.array(rows)[order], np.ones(len(rows)))
+
+
+def test_bc_path_graph_closed_form():
+    """On a path of n vertices every source counts vertex i as a shortest-path
+    interior exactly for the targets on its far side: summed over all sources,
+    bc(i) = 2 * i * (n - 1 - i)."""
+    from oracle import bc as obc
+    n = 9
+    A = _undirected(n, [(i, i + 1) for i in range(n - 1)])
+    bc, levels = obc.brandes(A, range(n))
+    assert np.allclose(bc, [2 * i * (n - 1 - i) for i in range(n)])
+    assert sum(levels) == n * n
+
+
+def test_bc_star_and_cycle():
+    """Star: the centre lies on every leaf-to-leaf path (bc = (n-1)(n-2) over
+    ordered pairs), leaves on none.  Cycle of 6: ordered pairs at distance 2
+    (12, one path, one interior vertex) give 12, pairs at distance 3 (6, two
+    paths of two interior vertices, weight 1/2 each) give 12; by symmetry each
+    vertex gets 24 / 6 = 4."""
+    from oracle import bc as obc
+    n = 7
+    A = _undirected(n, [(0, i) for i in range(1, n)])
+    bc, _ = obc.brandes(A, range(n))
+    assert np.isclose(bc[0], (n - 1) * (n - 2)) and np.allclose(bc[1:], 0)
+    C = _undirected(6, [(i, (i + 1) % 6) for i in range(6)])
+    bc, _ = obc.brandes(C, range(6))
+    assert np.allclose(bc, 4.0)
+
+
+def test_bc_matches_networkx_subset():
+    """A random graph and a subset of sources against networkx's subset
+    betweenness (sources x all targets), which for undirected graphs halves
+    the sum: ours = 2 * networkx."""
+    nx = pytest.importorskip("networkx")
+    from oracle import bc as obc
+    rng = np.random.default_rng(4)
+    n = 60
+    edges = {(int(a), int(b)) for a, b in rng.integers(0, n, (150, 2)) if a != b}
+    edges = {(min(a, b), max(a, b)) for a, b in edges}
+    A = _undirected(n, sorted(edges))
+    src = [0, 5, 17, 33, 59]
+    bc, _ = obc.brandes(A, src)
+    G = nx.Graph()
+    G.add_nodes_from(range(n))
+    G.add_edges_from(edges)
+    ref = nx.betweenness_centrality_subset(G, src, list(range(n)), normalized=False)
+    assert np.allclose(bc, 2 * np.array([ref[v] for v in range(n)]))
