@@ -359,6 +359,33 @@ spg_status spgemm_count_noalloc(const spg_csc *A, const spg_csc *B, int64_t *nnz
  * P < 1), SPG_UNSUPPORTED (int32 row ids of A with 2^31 or more non-empty
  * (i, j) pairs), and those of spgemm_1d_multiply.
  */
+/* ---------------------------------------------------------------------------
+ * Batched betweenness centrality (Section 3.2: Brandes' algorithm for a batch
+ * of sources, multi-source BFS forward search and backward sweep, each level
+ * one column 1D SpGEMM).  A: n x n device CSC of an unweighted graph, column v
+ * listing the neighbours of v (values ignored; symmetric for an undirected
+ * graph).  sources: s device int32 vertex ids (one frontier column each).
+ * opt: as for spgemm_1d_multiply (P, b, stream, allocator).  bc: n device
+ * doubles to which the batch adds sum over its sources of the Brandes
+ * dependency delta_s(v) (zero it before the first batch).  level_nnz (host,
+ * may be NULL): the (vertex, source) pairs reached at each BFS level, up to
+ * level_cap levels.  stats (host, may be NULL).  Intermediate frontiers live
+ * in memory from opt->alloc and are released before the call returns.
+ * Synchronises the stream.  Errors: SPG_INVALID_ARGUMENT (NULL pointers,
+ * non-square A, s < 0, a source outside [0, n)), and those of
+ * spgemm_1d_multiply.
+ */
+typedef struct {
+    int64_t levels;            /* BFS levels, the sources' own level included */
+    int64_t frontier_nnz;      /* (vertex, source) pairs reached over all levels */
+    int64_t products_forward;  /* sparse flops of the forward-search products */
+    int64_t products_backward; /* sparse flops of the backward-sweep products */
+    double ms_forward, ms_backward;
+} spg_bc_stats;
+
+spg_status spgemm_bc_batch(const spg_csc *A, const int32_t *sources, int32_t s, const spg_options *opt, double *bc,
+                           int64_t *level_nnz, int32_t level_cap, spg_bc_stats *stats);
+
 typedef struct {
     int64_t P;
     int64_t products;      /* sum_j flops_j of A * B */

@@ -343,6 +343,37 @@ def spgemm_outer_multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, 
     return DeviceCSC(c.nrows, c.ncols, colptr, rowidx, vals), {n: getattr(st, n) for n, _ in spg_outer_stats._fields_}
 
 
+class spg_bc_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "levels", "frontier_nnz", "products_forward", "products_backward")] + [
+        (name, ctypes.c_double) for name in ("ms_forward", "ms_backward")]
+
+
+def spgemm_bc_batch(A: DeviceCSC, sources: torch.Tensor, P=1, b=1024, bc: torch.Tensor | None = None, stream=None,
+                    validate=True, max_levels=256):
+    """Batched Brandes betweenness (Section 3.2): adds, for the given source
+    vertices (a CUDA int32 tensor), the dependencies delta_s(v) into bc (a CUDA
+    float64 tensor of n, zeros if not given).  Returns (bc, level sizes, stats)."""
+    lib = load_library()
+    lib.spgemm_bc_batch.argtypes = [ctypes.POINTER(spg_csc), ctypes.c_void_p, ctypes.c_int32,
+                                    ctypes.POINTER(spg_options), ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.c_int32, ctypes.POINTER(spg_bc_stats)]
+    lib.spgemm_bc_batch.restype = ctypes.c_int
+    dev = A.colptr.device
+    src = sources.to(device=dev, dtype=torch.int32).contiguous()
+    if bc is None:
+        bc = torch.zeros(A.ncols, dtype=torch.float64, device=dev)
+    alloc = _TorchAllocator(dev)
+    opts = make_options(P, b, stream, validate, allocator=alloc)
+    lv = (ctypes.c_int64 * max_levels)()
+    st = spg_bc_stats()
+    a = A.as_c()
+    _check(lib.spgemm_bc_batch(ctypes.byref(a), src.data_ptr(), int(src.numel()), ctypes.byref(opts), bc.data_ptr(),
+                               lv, max_levels, ctypes.byref(st)))
+    stats = {n: getattr(st, n) for n, _ in spg_bc_stats._fields_}
+    return bc, [int(lv[i]) for i in range(min(stats["levels"], max_levels))], stats
+
+
 def spgemm_plan_blocks(plan: Plan) -> dict:
     """Per-block diagnostics: bounds (P + 1), flops, gathered and remote A~
     nonzeros (P each, numpy int64), and cv_mem_a = mean remote / nnz(A) (the

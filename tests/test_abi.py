@@ -124,3 +124,19 @@ def test_split_and_block_argument_errors_need_no_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.spgemm_plan(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(h)) == g.SPG_INVALID_ARGUMENT
     assert "split" in g.spgemm_last_error()
+
+
+def test_bc_argument_errors_need_no_gpu(lib):
+    import paper_2408_14558_gb300 as g
+    A = g.spg_csc(4, 5, 0, 0, 0, 0, 0, 1, None, None)       # not square, no arrays
+    o = g.spg_options()
+    lib.spgemm_default_options(ctypes.byref(o))
+    f = lib.spgemm_bc_batch
+    f.argtypes = [ctypes.POINTER(g.spg_csc), ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(g.spg_options),
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    assert f(ctypes.byref(A), None, 0, ctypes.byref(o), None, None, 0, None) == g.SPG_INVALID_ARGUMENT
+    fake = ctypes.c_double(0.0)
+    assert f(ctypes.byref(A), None, 0, ctypes.byref(o), ctypes.addressof(fake), None, 0, None) == g.SPG_INVALID_ARGUMENT
+    A.nrows = 5
+    assert f(ctypes.byref(A), None, 3, ctypes.byref(o), ctypes.addressof(fake), None, 0, None) == g.SPG_INVALID_ARGUMENT
