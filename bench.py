@@ -54,7 +54,7 @@ def parse_args(argv=None):
                     help="where the clock samples and the tuning cache are written")
     ap.add_argument("--workload", default="rmat18",
                     choices=["rmat18", "uniform8192", "galerkin128", "galerkin_right", "similarity", "batched",
-                             "structure"],
+                             "structure", "bc"],
                     help="rmat18 is the headline; the others measure the remaining configurations")
     ap.add_argument("--rmat-scale", type=int, default=RMAT_SCALE,
                     help="R-MAT scale of the rmat18 workload (smaller scales for profiler captures)")

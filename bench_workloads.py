@@ -293,6 +293,26 @@ def run_structure(args, torch, g, synth):
                      "per owner over nnz(A)"))
 
 
+def run_bc(args, torch, g, synth):
+    """One batch of the batched betweenness centrality (Section 3.2) on the
+    R-MAT scale-18 graph: 4096 random sources (the paper's batch size),
+    forward search and backward sweep, P = 16, b = 1024."""
+    A = synth.rmat_symmetric(18, 16, seed=0)
+    dA = g.to_device(A, ptr_dtype=torch.int32, idx_dtype=torch.int32)
+    src = torch.from_numpy(np.random.default_rng(0).choice(A.ncols, 4096, replace=False).astype(np.int32))
+    timed = _timer(torch)
+    res = timed(lambda: g.spgemm_bc_batch(dA, src, P=16, b=1024, validate=False), max(args.steps, 2),
+                max(args.warmup, 1))
+    ms = statistics.median(t for t, _ in res)
+    _, levels, st = res[0][1]
+    prods = st["products_forward"] + st["products_backward"]
+    _emit(_base("bc_rmat_s18_ef16_batch4096_P16_b1024", "betweenness batch GFLOP/s (forward search + backward "
+                "sweep SpGEMMs)", 2 * prods / (ms / 1e3) / 1e9, ms, max(args.steps, 2), max(args.warmup, 1), "f64",
+                {"sources": 4096, "levels": st["levels"], "frontier_nnz": st["frontier_nnz"],
+                 "products_forward": st["products_forward"], "products_backward": st["products_backward"]},
+                level_nnz=levels, ms_forward=st["ms_forward"], ms_backward=st["ms_backward"]))
+
+
 def run(args):
     import torch
     sys.path.insert(0, ROOT)
@@ -300,6 +320,7 @@ def run(args):
     import synth
     g.load_library()
     fn = {"uniform8192": run_uniform, "galerkin128": run_galerkin, "galerkin_right": run_galerkin_right,
-          "similarity": run_similarity, "batched": run_batched, "structure": run_structure}[args.workload]
+          "similarity": run_similarity, "batched": run_batched, "structure": run_structure,
+          "bc": run_bc}[args.workload]
     fn(args, torch, g, synth)
     return 0
