@@ -177,22 +177,6 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
             // (the first barrier of cta_products orders the zeroing before
             // every product)
             for (int i = tid; i < cnt; i += blockDim.x) acc[i] = Acc(0);
-#if SPG_EARLY_ROWS
-            // the row ids are known now: each thread writes the rows of its
-            // bitmap words while the products are still ahead
-            {
-                const int64_t rbase = (int64_t)t0 * R;
-                for (int w = tid; w < nwords; w += blockDim.x) {
-                    uint32_t word = bp[w].x;
-                    int64_t pos = h.cbase + bp[w].y;
-                    while (word) {
-                        int bb = __ffs(word) - 1;
-                        st_stream(Crow + pos++, (OutIdx)(rbase + w * 32 + bb));
-                        word &= word - 1u;
-                    }
-                }
-            }
-#endif
             const int wbase = t0 * RW;
             bool miss = false;
             cta_products<true, SPG_NUM_UNROLL, Acc>(
@@ -216,7 +200,6 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
             if (tid == 0 && (long long)nxt < nitems) nh = items[nxt];
             // cta_products ends with a barrier: acc is complete
             for (int i = tid; i < cnt; i += blockDim.x) st_stream(Cval + h.cbase + i, acc[i]);
-#if !SPG_EARLY_ROWS
             __syncthreads();
             // the row ids go to shared memory by rank first (over the consumed
             // values: cnt ints fit in cnt Accs), then to C in one coalesced run
@@ -233,7 +216,6 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
             __syncthreads();
             const int64_t rbase = (int64_t)t0 * R;
             for (int i = tid; i < cnt; i += blockDim.x) st_stream(Crow + h.cbase + i, (OutIdx)(rbase + srow[i]));
-#endif
         } else {
             // the item's room in C was sized from the record counts: never
             // write past it

@@ -363,12 +363,6 @@ __device__ __forceinline__ T ld_stream(const T *p) {
 #endif
 }
 
-// k_num_heavy writes an item's row ids right after its bitmap scan (1) or
-// stages them in shared memory after the products (0).
-#ifndef SPG_EARLY_ROWS
-#define SPG_EARLY_ROWS 0
-#endif
-
 // Set bit b of a shared bitmap word; with SPG_TEST_FIRST the word is read
 // first and the atomic skipped when the bit is already set (bits are only ever
 // set during a pass, so a stale read can only cause a redundant atomic).
