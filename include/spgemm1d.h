@@ -175,6 +175,22 @@ spg_status spgemm_numeric(spg_plan *plan, spg_csc *C);
  */
 spg_status spgemm_1d_multiply(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C);
 
+/*
+ * Repeated products with fixed patterns (an extension beyond the paper):
+ * after one spgemm_numeric on the plan, new values in A's and B's value
+ * arrays (same pointers, same patterns) are taken up by
+ * spgemm_numeric_refresh, which re-gathers A~'s values, re-maps B's and runs
+ * the numeric pass into C (C->colptr as for spgemm_numeric).  It only
+ * launches kernels, so spgemm_plan_capture can record it once as a CUDA graph
+ * (on the plan's stream, which must not be the legacy default stream; C's
+ * arrays are captured by address) and spgemm_plan_replay launches that graph.
+ * Errors: SPG_INVALID_ARGUMENT (NULL pointers, no numeric pass yet, nothing
+ * captured), SPG_CUDA_ERROR.
+ */
+spg_status spgemm_numeric_refresh(spg_plan *plan, spg_csc *C);
+spg_status spgemm_plan_capture(spg_plan *plan, spg_csc *C);
+spg_status spgemm_plan_replay(spg_plan *plan);
+
 /* Copy the plan's counters into *st (host).  Synchronises the stream. */
 spg_status spgemm_plan_stats(const spg_plan *plan, spg_stats *st);
 

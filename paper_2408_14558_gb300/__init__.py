@@ -273,6 +273,31 @@ def spgemm_numeric(plan: Plan, colptr: torch.Tensor | None = None) -> DeviceCSC:
     return DeviceCSC(plan.A.nrows, plan.B.ncols, colptr, rowidx, vals)
 
 
+def _c_out(C: DeviceCSC) -> spg_csc:
+    return spg_csc(0, 0, 0, 0, 0, 0, 0, C.colptr.data_ptr(), C.rowidx.data_ptr() if C.nnz else None,
+                   C.vals.data_ptr() if C.nnz else None)
+
+
+def spgemm_numeric_refresh(plan: Plan, C: DeviceCSC) -> DeviceCSC:
+    """Recompute C in place after new values were written into the plan's A
+    and B tensors (same patterns); needs one spgemm_numeric on the plan."""
+    c = _c_out(C)
+    _check(load_library().spgemm_numeric_refresh(plan.handle, ctypes.byref(c)))
+    return C
+
+
+def spgemm_plan_capture(plan: Plan, C: DeviceCSC):
+    """Record spgemm_numeric_refresh(plan, C) as a CUDA graph on the plan's
+    stream (create the plan on a non-default stream)."""
+    c = _c_out(C)
+    plan._graph_out = C            # the graph writes into C's arrays
+    _check(load_library().spgemm_plan_capture(plan.handle, ctypes.byref(c)))
+
+
+def spgemm_plan_replay(plan: Plan):
+    _check(load_library().spgemm_plan_replay(plan.handle))
+
+
 def spgemm_plan_stats(plan: Plan) -> dict:
     lib = load_library()
     st = spg_stats()

@@ -73,7 +73,63 @@ extern "C" spg_status spgemm_numeric(spg_plan *p, spg_csc *C) {
     C->ptr_type = SPG_IDX_I64;
     C->idx_type = p->out_idx64 ? SPG_IDX_I64 : SPG_IDX_I32;
     C->val_type = p->acc_f64 ? SPG_VAL_F64 : SPG_VAL_I64;
-    return run_numeric(p, C);
+    spg_status s = run_numeric(p, C);
+    if (!s) p->numeric_done = true;
+    return s;
+}
+
+extern "C" spg_status spgemm_numeric_refresh(spg_plan *p, spg_csc *C) {
+    clear_error();
+    if (!p || !C) {
+        set_error("plan and C must not be NULL");
+        return SPG_INVALID_ARGUMENT;
+    }
+    if (!p->numeric_done) {
+        set_error("spgemm_numeric must have run once on this plan before a refresh");
+        return SPG_INVALID_ARGUMENT;
+    }
+    spg_status s = copy_operands(p);
+    if (!s) s = spgemm_numeric(p, C);
+    return s;
+}
+
+extern "C" spg_status spgemm_plan_capture(spg_plan *p, spg_csc *C) {
+    clear_error();
+    if (!p || !C) {
+        set_error("plan and C must not be NULL");
+        return SPG_INVALID_ARGUMENT;
+    }
+    if (!p->numeric_done) {
+        set_error("spgemm_numeric must have run once on this plan before a capture");
+        return SPG_INVALID_ARGUMENT;
+    }
+    spg_status s = cuda_check(cudaStreamSynchronize(p->st), "capture");
+    if (s) return s;
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph_exec = nullptr;
+    p->graph = nullptr;
+    s = cuda_check(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal), "capture (the plan's stream must not be the legacy default stream)");
+    if (s) return s;
+    spg_status sr = spgemm_numeric_refresh(p, C);
+    cudaGraph_t g = nullptr;
+    s = cuda_check(cudaStreamEndCapture(p->st, &g), "end capture");
+    if (sr) {
+        if (g) cudaGraphDestroy(g);
+        return sr;
+    }
+    if (s) return s;
+    p->graph = g;
+    return cuda_check(cudaGraphInstantiate(&p->graph_exec, g, 0), "graph instantiate");
+}
+
+extern "C" spg_status spgemm_plan_replay(spg_plan *p) {
+    clear_error();
+    if (!p || !p->graph_exec) {
+        set_error("no captured graph on this plan (spgemm_plan_capture)");
+        return SPG_INVALID_ARGUMENT;
+    }
+    return cuda_check(cudaGraphLaunch(p->graph_exec, p->st), "graph launch");
 }
 
 extern "C" spg_status spgemm_plan_stats(const spg_plan *pc, spg_stats *st) {

@@ -733,6 +733,49 @@ __global__ void k_split(const int64_t *At_colptr, const int32_t *At_row, int64_t
 
 // ------------------------------------------------------------------ host
 
+// Step 3 and the remap of B: A~ = A(:, D~) (rows and values, entry-balanced)
+// and B's entries as (column of A~, value).  Launches only, so that
+// spgemm_numeric_refresh can re-run it (new values, same patterns) inside a
+// captured graph; its scratch is allocated once.
+spg_status copy_operands(spg_plan *p) {
+    const spg_csc &A = p->A, &B = p->B;
+    const int sm = p->sm_count, P = p->P;
+    const int64_t n = p->n, W = p->W;
+    const int p64A = A.ptr_type == SPG_IDX_I64, i64A = A.idx_type == SPG_IDX_I64;
+    const int p64B = B.ptr_type == SPG_IDX_I64, i64B = B.idx_type == SPG_IDX_I64;
+    if (p->ndt > 0 && p->nAt > 0) {
+        if (!p->gshift) p->gshift = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)p->ndt);
+        if (!p->gshift) return SPG_OUT_OF_MEMORY;
+        // about 2048 entries per warp, at most 32 CTAs of 8 warps per SM
+        const int64_t warps = std::max<int64_t>(1, std::min<int64_t>((p->nAt + 2047) / 2048, (int64_t)sm * 32 * 8));
+        const int64_t chunk = ((p->nAt + warps - 1) / warps + 31) & ~(int64_t)31;
+        const int64_t g = (((p->nAt + chunk - 1) / chunk) + 7) / 8;
+        group_begin(p, kKGather);
+        launch(p, k_gather_shift, grid_for(p->ndt, 256, sm * 8), 256, 0, p->dtilde, p->ndt, A.colptr, p64A,
+               p->At_colptr, p->gshift);
+        if (p->acc_f64)
+            launch(p, k_gather_copy<double>, (unsigned)g, 256, 0, p->At_colptr, p->gshift, p->ndt, p->nAt, chunk,
+                   A.rowidx, i64A, A.vals, A.val_type, p->At_row, (double *)p->At_val);
+        else
+            launch(p, k_gather_copy<long long>, (unsigned)g, 256, 0, p->At_colptr, p->gshift, p->ndt, p->nAt, chunk,
+                   A.rowidx, i64A, A.vals, A.val_type, p->At_row, (long long *)p->At_val);
+        group_end(p, kKGather);
+        spg_status s = cuda_check(cudaGetLastError(), "gather");
+        if (s) return s;
+    }
+    if (n > 0) {
+        int g = grid_for(n * 32, 256, sm * 16);
+        if (p->acc_f64)
+            launch(p, k_remap_B<double>, g, 256, 0, B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P, p->Hbits,
+                   p->Dbits, p->rankpre, W, p->Bq, (double *)p->Bv, p->bounds_d);
+        else
+            launch(p, k_remap_B<long long>, g, 256, 0, B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P,
+                   p->Hbits, p->Dbits, p->rankpre, W, p->Bq, (long long *)p->Bv, p->bounds_d);
+        return cuda_check(cudaGetLastError(), "remap B");
+    }
+    return SPG_OK;
+}
+
 static bool valid_type(int32_t v, int maxv) { return v >= 0 && v <= maxv; }
 
 static spg_status check_csc(const spg_csc *M, const char *name) {
@@ -883,36 +926,7 @@ static spg_status plan_build(spg_plan *p) {
     p->Bq = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(p->nnzB + 1));
     p->Bv = ws_alloc(p, accsz * (size_t)(p->nnzB + 1));
     if (!p->At_row || !p->At_val || !p->Bq || !p->Bv) return SPG_OUT_OF_MEMORY;
-    if (p->ndt > 0 && p->nAt > 0) {
-        int64_t *shift = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)p->ndt);
-        if (!shift) return SPG_OUT_OF_MEMORY;
-        // about 2048 entries per warp, at most 32 CTAs of 8 warps per SM
-        const int64_t warps = std::max<int64_t>(1, std::min<int64_t>((p->nAt + 2047) / 2048, (int64_t)sm * 32 * 8));
-        const int64_t chunk = ((p->nAt + warps - 1) / warps + 31) & ~(int64_t)31;
-        const int64_t g = (((p->nAt + chunk - 1) / chunk) + 7) / 8;
-        group_begin(p, kKGather);
-        launch(p, k_gather_shift, grid_for(p->ndt, 256, sm * 8), 256, 0, p->dtilde, p->ndt, A.colptr, p64A,
-               p->At_colptr, shift);
-        if (p->acc_f64)
-            launch(p, k_gather_copy<double>, (unsigned)g, 256, 0, p->At_colptr, shift, p->ndt, p->nAt, chunk,
-                   A.rowidx, i64A, A.vals, A.val_type, p->At_row, (double *)p->At_val);
-        else
-            launch(p, k_gather_copy<long long>, (unsigned)g, 256, 0, p->At_colptr, shift, p->ndt, p->nAt, chunk,
-                   A.rowidx, i64A, A.vals, A.val_type, p->At_row, (long long *)p->At_val);
-        group_end(p, kKGather);
-        LAUNCH_OK("gather");
-    }
-    if (n > 0) {
-        int g = grid_for(n * 32, 256, sm * 16);
-        if (p->acc_f64)
-            launch(p, k_remap_B<double>, g, 256, 0, B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P, p->Hbits,
-                                                 p->Dbits, p->rankpre, W, p->Bq, (double *)p->Bv, p->bounds_d);
-        else
-            launch(p, k_remap_B<long long>, g, 256, 0, B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P,
-                                                    p->Hbits, p->Dbits, p->rankpre, W, p->Bq, (long long *)p->Bv,
-                                                    p->bounds_d);
-        LAUNCH_OK("remap B");
-    }
+    TRY(copy_operands(p));
 
     // --- step 4: flops, windows, bins
     p->flops = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(n + 1));
@@ -1117,6 +1131,9 @@ extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_
 
 extern "C" spg_status spgemm_plan_destroy(spg_plan *p) {
     if (!p) return SPG_OK;
+    cudaStreamSynchronize(p->st);
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
     ws_free_all(p);
     cudaStreamSynchronize(p->st);
     for (int i = 0; i < 8; i++)

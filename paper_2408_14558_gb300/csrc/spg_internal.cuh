@@ -123,6 +123,10 @@ struct spg_plan {
     int64_t *bounds_d = nullptr;     // column block bounds (P + 1) of a non-uniform split, else null
     std::vector<int64_t> bounds_h;   // the bounds in effect (P + 1), host
     int64_t *blk = nullptr;          // per block: flops, gathered A~ nonzeros, of them fetched (3 x P)
+    int64_t *gshift = nullptr;       // per A~ column: its entries' offset into A (gather)
+    bool numeric_done = false;       // a numeric pass ran: the light lists and item headers exist
+    cudaGraph_t graph = nullptr;     // captured refresh + numeric (spgemm_plan_capture)
+    cudaGraphExec_t graph_exec = nullptr;
     int64_t nbin_off[spg::kNumBins + 1] = {0};
 
     spg_stats stats{};
@@ -174,6 +178,7 @@ void set_error(const char *fmt, ...);
 spg_status cuda_check(cudaError_t e, const char *what);
 void *ws_alloc(spg_plan *p, size_t bytes);
 void ws_free_all(spg_plan *p);
+spg_status copy_operands(spg_plan *p);
 // Memory handed to the caller (C's arrays): through opt->alloc, else cudaMallocAsync.
 void *alloc_user(const spg_options *opt, size_t bytes);
 spg_status read_dev_err(spg_plan *p, const char *phase);
