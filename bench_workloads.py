@@ -8,8 +8,16 @@ the same C ABI (`python bench.py --workload NAME`); one JSON line each.
     batched      512 independent ER / R-MAT-row products (n log-uniform in
                  [1000, 200000], 4..32 per column, f64): one persistent graph
                  launch vs 512 sequential spgemm_1d_multiply calls
+    galerkin_right  (R^T A) R by the column 1D path and the outer-product 1D path
+    structure    CV/memA and block balance: ordering x column split
+    bc           one 4096-source betweenness batch on the R-MAT scale-18 graph
 Every timed region is bracketed by CUDA events on the library's stream, after
-warm-up, with a 256 MiB write that evicts L2 before each timed step.
+warm-up, with a 256 MiB write that evicts L2 before each timed step.  Each line
+carries a ``roofline`` object for its dominant phase (the library's own event
+times per phase, priced in algorithmic bytes: 12 B per nonzero read or written,
+8 B per output column pointer) against the measured HBM copy bandwidth, and a
+``cpu_baseline``: the oracle on the host cores on a bounded sample of the same
+workload.
 """
 from __future__ import annotations
 
@@ -23,6 +31,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 FLUSH_BYTES = 256 << 20
+SIM_SAMPLE_COLS = 4096        # columns of A*A^T the oracle computes for the CPU baseline
+BATCH_SAMPLE = 32             # instances of the batched workload the oracle computes
+BC_SAMPLE_SOURCES = 2         # sources of the betweenness batch the oracle computes
 
 
 def _emit(line):
@@ -56,6 +67,68 @@ def _base(workload, metric, value, ms, steps, warmup, dtype, config, **extra):
             "data": "synthetic", "config": dict(workload=workload, **config)}
     line.update(extra)
     return line
+
+
+_PHASES = ("num_heavy", "num_light", "sym_heavy", "sym_light", "gather")
+
+
+def _roofline(groups, kernel_names=None, note=None):
+    """groups: {name: (algorithmic bytes, milliseconds)} summed over the
+    multiplies of one step.  The dominant group (largest time) is reported:
+    achieved = its bytes / its time, against the measured HBM copy bandwidth."""
+    import bench
+    peak, src = bench.measured_peak_hbm()
+    name = max(groups, key=lambda k: groups[k][1])
+    by, ms = groups[name]
+    achieved = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    r = {"bound": "hbm", "kernel": (kernel_names or {}).get(name, name), "achieved": achieved, "peak": peak,
+         "unit": "GB/s", "frac": achieved / peak, "traffic": None, "algorithmic_bytes_per_step": by,
+         "ms_per_step": ms, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+         "phase_ms": {k: v[1] for k, v in groups.items()}}
+    if note:
+        r["note"] = note
+    return r
+
+
+_KERNELS = {"num_heavy": "k_num_heavy", "num_light": "k_num_light", "sym_heavy": "k_sym_heavy",
+            "sym_light": "k_sym_light", "gather": "k_gather_copy"}
+
+
+def _column_groups(stats):
+    """Per-phase (bytes, ms) of column-1D multiplies from their plan stats."""
+    import bench
+    out = {}
+    for st in stats:
+        for ph in _PHASES:
+            by, ms = out.get(ph, (0.0, 0.0))
+            out[ph] = (by + bench.kernel_bytes(ph, st), ms + st["ms_" + ph])
+    return out
+
+
+def _cpu_baseline(args, fn, sample, cores=None, min_seconds=3.0):
+    """Time fn() (the oracle on a sample; it returns the sample's product
+    count), repeated until min_seconds have passed; value = 2 * products /
+    seconds in GFLOP/s."""
+    if getattr(args, "no_cpu_baseline", False):
+        return None
+    import oracle
+    products, reps = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        products += int(fn())
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_seconds:
+            break
+    rep = f" x {reps} repetitions" if reps > 1 else ""
+    return {"value": 2.0 * products / dt / 1e9, "unit": "GFLOP/s",
+            "cores": oracle.max_threads() if cores is None else cores, "kind": "oracle",
+            "sample": f"{sample}{rep}: {products} products, {dt:.2f} s", "seconds": dt}
+
+
+def _csc(synth, r):
+    """A synth.CSC from an oracle result dict."""
+    return synth.CSC(int(r["nrows"]), int(r["ncols"]), r["colptr"], r["rowidx"], r["vals"])
 
 
 def _graph_replay_ms(torch, g, dA, dB, P, b, reps=200):
@@ -94,8 +167,13 @@ def run_uniform(args, torch, g, synth):
     res = timed(step, max(args.steps, 20), max(args.warmup, 5))
     ms = statistics.median(t for t, _ in res)
     st = res[0][1]
+    import oracle
+    cpu = _cpu_baseline(args, lambda: oracle.spgemm(A, A)["flops"].sum(), "the whole product")
     _emit(_base("uniform8192_d8_P4_b256", "C=A·A GFLOP/s", 2 * st["products"] / (ms / 1e3) / 1e9, ms, len(res),
                 max(args.warmup, 5), "f64", {"products": st["products"], "nnzC": st["nnzC"]},
+                roofline=_roofline(_column_groups([st]), _KERNELS,
+                                   note="the multiply is launch bound: compare phase_ms with ms_per_step"),
+                cpu_baseline=cpu,
                 phase_ms={k: st["ms_" + k] for k in ("plan", "symbolic", "numeric")},
                 gpu_launches=st["kernel_launches"], l2="flushed before every timed step",
                 graph_replay_ms=_graph_replay_ms(torch, g, dA, dA, 4, 256),
@@ -125,9 +203,18 @@ def run_galerkin(args, torch, g, synth):
     ms = statistics.median(t for t, _ in res)
     s1, s2 = res[0][1]
     prods = s1["products"] + s2["products"]
+    import oracle
+
+    def cpu_run():
+        r1 = oracle.spgemm(A, Pg)
+        r2 = oracle.spgemm(PT, _csc(synth, r1))
+        return r1["flops"].sum() + r2["flops"].sum()
+    cpu = _cpu_baseline(args, cpu_run, "both products in full")
     _emit(_base("galerkin_7pt_128cube_P32_b2048", "P^T(A P) GFLOP/s", 2 * prods / (ms / 1e3) / 1e9, ms, len(res),
                 max(args.warmup, 3), "f64",
                 {"products": [s1["products"], s2["products"]], "nnzC": [s1["nnzC"], s2["nnzC"]]},
+                roofline=_roofline(_column_groups([s1, s2]), _KERNELS), cpu_baseline=cpu,
+                gpu_launches=s1["kernel_launches"] + s2["kernel_launches"],
                 phase_ms=[{k: s["ms_" + k] for k in ("plan", "symbolic", "numeric")} for s in (s1, s2)],
                 gathered_nnz=[s1["gathered_nnz_exact"], s2["gathered_nnz_exact"]],
                 fetch_blocks=[[s["fetch_blocks_chosen"], s["fetch_blocks_total"]] for s in (s1, s2)],
@@ -177,9 +264,18 @@ def run_similarity(args, torch, g, synth):
                       "learned_speedup": ms_exact / ms_l, "recomputed_columns": rec,
                       "recompute_rate": rec / n, "capacity_over_nnz": cap / nnzc})
         value, ms = extra["learned_gflops"], ms_l
+        extra["roofline"] = _roofline(_column_groups(st), {**_KERNELS, "num_heavy": "k_fused_heavy"},
+                                      note="learned sizing: the heavy phase is the fused pattern + value pass")
     else:
         extra["learned"] = "no model file: run python -m paper_2408_14558_gb300.learned"
         value, ms = extra["exact_gflops"], ms_exact
+        extra["roofline"] = _roofline(_column_groups(ex[0][1]), _KERNELS)
+    extra["roofline_exact"] = _roofline(_column_groups(ex[0][1]), _KERNELS)
+    import oracle
+    cols = np.sort(np.random.default_rng(0).choice(At.ncols, SIM_SAMPLE_COLS, replace=False))
+    extra["cpu_baseline"] = _cpu_baseline(args, lambda: oracle.spgemm(A, At, cols=cols)["flops"].sum(),
+                                          f"{SIM_SAMPLE_COLS} random columns of C (seed 0)")
+    extra["gpu_launches"] = sum(s_["kernel_launches"] for s_ in (le[0][1] if model is not None else ex[0][1]))
     _emit(_base("similarity_AAt_100k_x_1M_lognormal_zipf", "C=A·Aᵀ GFLOP/s (learned sizing; exact alongside)",
                 value, ms, max(args.steps, 2), max(args.warmup, 1), "int64",
                 {"nnzA": A.nnz, "products": prods, "nnzC": nnzc, "column_chunks": chunks, "P": P, "b": 1024},
@@ -209,20 +305,30 @@ def run_batched(args, torch, g, synth):
     ms_b = statistics.median(t for t, _ in res)
 
     def run_seq():
-        prods = 0
+        prods, nbytes = 0, 0.0
         for A, B in zip(As, Bs):
             C, _ = g.spgemm_1d_multiply(A, B, P=1, b=1024)
-            prods += g.spgemm_last_multiply_stats()["products"]
+            st = g.spgemm_last_multiply_stats()
+            prods += st["products"]
+            nbytes += bench.compulsory_bytes(st)
             del C
-        return prods
+        return prods, nbytes
+    import bench
     seq = timed(run_seq, 2, 1)
     ms_s = statistics.median(t for t, _ in seq)
-    prods = seq[0][1]
+    prods, nbytes = seq[0][1]
     info = g.spgemm_batch_info(batch)
+    import oracle
+    pick = np.sort(np.random.default_rng(0).choice(len(pairs), BATCH_SAMPLE, replace=False))
+    cpu = _cpu_baseline(args, lambda: sum(int(oracle.spgemm(*pairs[i])["flops"].sum()) for i in pick),
+                        f"{BATCH_SAMPLE} random instances (seed 0)")
+    roof = _roofline({"batch": (nbytes, ms_b)}, {"batch": "k_batch_persistent (3 table classes, one graph)"},
+                     note="bytes: every instance's B, gathered A columns and C once; time: the whole graph launch")
     _emit(_base("batched_512_er_rmat_n1e3_2e5_d4_32", "batched C_j=A_j·B_j GFLOP/s (one persistent graph launch)",
                 2 * prods / (ms_b / 1e3) / 1e9, ms_b, len(res), max(args.warmup, 2), "f64",
                 {"instances": 512, "products": prods, "tuned": tune, "tasks": info["tasks"],
                  "grid": info["grid"], "pool_entries": info["pool_entries"]},
+                roofline=roof, cpu_baseline=cpu,
                 sequential_ms=ms_s, sequential_gflops=2 * prods / (ms_s / 1e3) / 1e9, speedup_vs_sequential=ms_s / ms_b,
                 batch_create_ms=create_ms, generation_s=gen_s))
 
@@ -269,10 +375,26 @@ def run_galerkin_right(args, torch, g, synth):
                       "outer_1d_moved_partial_entries": so["partial_moved"],
                       "outer_1d_partial_nnz": so["partial_nnz"],
                       "outer_1d_ms_split_local_merge": [so["ms_split"], so["ms_local"], so["ms_merge"]]}
+        if order == "lexicographic":
+            nnz_a, nnz_b, n = int(RtA.colptr[-1]), int(dR.colptr[-1]), dR.ncols
+            roof_outer = _roofline(
+                {"split": (2 * 12 * nnz_b, so["ms_split"]),
+                 "local": (12 * (nnz_a + nnz_b + so["partial_nnz"]), so["ms_local"]),
+                 "merge": (12 * (so["partial_nnz"] + so["nnzC"]) + 8 * (n + 1), so["ms_merge"])},
+                {"split": "k_outer_count + k_outer_copy", "local": "column 1D kernels on A * B'",
+                 "merge": "column 1D kernels on C' * S"},
+                note="split: B read and written once; local: A, the row-split B and the partial columns once; "
+                     "merge: partial columns read, C written")
+            roof_col = _roofline(_column_groups([sc]), _KERNELS)
+    import oracle
+    RtA_h = _csc(synth, oracle.spgemm(RT, A))
+    cpu = _cpu_baseline(args, lambda: oracle.spgemm(RtA_h, R)["flops"].sum(),
+                        "(R^T A) R in full, lexicographic ordering")
     lex = out["lexicographic"]
     _emit(_base("galerkin_right_RtA_R_128cube_P32_b2048", "(R^T A) R GFLOP/s, column 1D vs outer-product 1D",
                 lex["outer_1d_gflops"], lex["outer_1d_ms"], max(args.steps, 5), max(args.warmup, 3), "f64",
                 {"nnzC": 7 * (N // 2) ** 3 - 6 * (N // 2) ** 2}, orderings=out,
+                roofline=roof_outer, roofline_column_1d=roof_col, cpu_baseline=cpu,
                 note="value = outer-product path, lexicographic ordering; moved/fetched entries are what a "
                      "32-owner distributed run would transfer"))
 
@@ -286,10 +408,11 @@ def run_structure(args, torch, g, synth):
     over the mean, and the multiply's time on this GPU."""
     P, b = 16, 1024
     timed = _timer(torch)
-    rows = []
+    rows, host, stats = [], {}, []
     for name, A in (("poisson3d_128", synth.poisson3d(128)), ("rmat_s18_ef16", synth.rmat_symmetric(18, 16, seed=0))):
         q = synth.random_permutation(A.ncols, seed=2)
         for order, M in (("original", A), ("permuted", synth.relabel(A, q, q))):
+            host[(name, order)] = M
             dM = g.to_device(M, ptr_dtype=torch.int32, idx_dtype=torch.int32)
             for split_name, split in (("uniform", g.SPG_SPLIT_UNIFORM), ("flops", g.SPG_SPLIT_FLOPS)):
                 def step():
@@ -310,10 +433,20 @@ def run_structure(args, torch, g, synth):
                              "fetch_blocks_chosen": st["fetch_blocks_chosen"],
                              "gathered_block_volume": st["gathered_nnz_block"], "nnzA": int(M.rowidx.size),
                              "block_flops_max_over_mean": float(fl.max() / max(fl.mean(), 1))})
-    best = max(r["gflops"] for r in rows)
+                stats.append(st)
+    ib = max(range(len(rows)), key=lambda i: rows[i]["gflops"])
+    best = rows[ib]["gflops"]
+    import oracle
+    M = host[(rows[ib]["matrix"], rows[ib]["ordering"])]
+    cols = np.sort(np.random.default_rng(0).choice(M.ncols, min(M.ncols, 65536), replace=False))
+    cpu = _cpu_baseline(args, lambda: oracle.spgemm(M, M, cols=cols)["flops"].sum(),
+                        f"{cols.size} random columns (seed 0) of the fastest case's product")
     _emit(_base("structure_AxA_poisson128_rmat18_P16_b1024", "CV/memA and block balance, original vs permuted "
-                "ordering, uniform vs flop split", best, min(r["ms"] for r in rows), max(args.steps, 3),
+                "ordering, uniform vs flop split", best, rows[ib]["ms"], max(args.steps, 3),
                 max(args.warmup, 2), "f64", {"P": P, "b": b}, cases=rows,
+                roofline=dict(_roofline(_column_groups([stats[ib]]), _KERNELS),
+                              case=f"{rows[ib]['matrix']} {rows[ib]['ordering']} {rows[ib]['split']}"),
+                cpu_baseline=cpu,
                 note="value = best GFLOP/s of the cases; cv_mem_a is what a 16-owner distributed run would fetch "
                      "per owner over nnz(A)"))
 
@@ -331,11 +464,27 @@ def run_bc(args, torch, g, synth):
     ms = statistics.median(t for t, _ in res)
     _, levels, st = res[0][1]
     prods = st["products_forward"] + st["products_backward"]
+    # algorithmic bytes: every level's product reads A once, its input frontier
+    # (or dependency weights) and writes the masked next frontier (or the
+    # previous level's dependencies); 12 B per nonzero
+    lv = list(levels) + [0]
+    fwd = sum(12 * (A.nnz + lv[l] + lv[l + 1]) for l in range(len(levels)))
+    bwd = sum(12 * (A.nnz + lv[l] + lv[l - 1]) for l in range(1, len(levels)))
+    roof = _roofline({"forward": (fwd, st["ms_forward"]), "backward": (bwd, st["ms_backward"])},
+                     {"forward": "forward search SpGEMMs (column 1D path + frontier mask)",
+                      "backward": "backward sweep SpGEMMs (column 1D path + dependency update)"})
+    from oracle import bc as obc
+    srcs = src.numpy()[:BC_SAMPLE_SOURCES]
+    per_source = prods / 4096.0
+    cpu = _cpu_baseline(args, lambda: (obc.brandes(A, srcs), per_source * len(srcs))[1],
+                        f"{len(srcs)} of the sources, Brandes in plain Python; products = the batch's SpGEMM "
+                        f"products per source x sources", cores=1)
     _emit(_base("bc_rmat_s18_ef16_batch4096_P16_b1024", "betweenness batch GFLOP/s (forward search + backward "
                 "sweep SpGEMMs)", 2 * prods / (ms / 1e3) / 1e9, ms, max(args.steps, 2), max(args.warmup, 1), "f64",
                 {"sources": 4096, "levels": st["levels"], "frontier_nnz": st["frontier_nnz"],
                  "products_forward": st["products_forward"], "products_backward": st["products_backward"]},
-                level_nnz=levels, ms_forward=st["ms_forward"], ms_backward=st["ms_backward"]))
+                level_nnz=levels, ms_forward=st["ms_forward"], ms_backward=st["ms_backward"],
+                roofline=roof, cpu_baseline=cpu))
 
 
 def run(args):

@@ -393,16 +393,24 @@ __global__ void k_count_groups(int64_t nheavy, const int64_t *rec_first, int per
 // fill counter, light ones from the kernel; overflowed columns get 0 here and
 // their exact count later.
 __global__ void k_learned_nnz(int64_t n, const int8_t *bin_of, const unsigned long long *colfill,
-                              const int64_t *nnz_light, const int32_t *flag, int64_t *nnz) {
+                              const int64_t *nnz_light, const int32_t *flag, int64_t *nnz,
+                              unsigned long long *heavy_sum) {
+    unsigned long long hsum = 0;  // entries of the heavy columns the fused pass completed
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         const int b = bin_of[j];
         int64_t v = 0;
         if (!flag[j]) {
-            if (b == kBinHeavy) v = (int64_t)colfill[j];
-            else if (b != kBinEmpty) v = nnz_light[j];
+            if (b == kBinHeavy) {
+                v = (int64_t)colfill[j];
+                hsum += (unsigned long long)v;
+            } else if (b != kBinEmpty) {
+                v = nnz_light[j];
+            }
         }
         nnz[j] = v;
     }
+    for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, o);
+    if ((threadIdx.x & 31) == 0 && hsum) atomicAdd(heavy_sum, hsum);
 }
 
 // Position of every flagged column in the list of flagged columns.
@@ -798,6 +806,9 @@ struct LearnedState {
 template <typename Acc, typename OutIdx>
 static spg_status learned_kernels(spg_plan *p, LearnedState &L) {
     spg_status s = SPG_OK;
+    // light columns and the fused heavy pass are timed as the light and heavy
+    // numeric groups
+    group_begin(p, kKNumLight);
     for (int bin = 1; bin <= kMaxLightBin && !s; bin++) {
         int64_t cnt = L.loff[bin + 1] - L.loff[bin];
         if (!cnt) continue;
@@ -811,6 +822,7 @@ static spg_status learned_kernels(spg_plan *p, LearnedState &L) {
             default: s = launch_light_learned<11, 4, Acc, OutIdx>(p, list, cnt, L.capoff, L.cap, L.nnz_light, L.flag, L.nflag, L.trow, L.tval); break;
         }
     }
+    group_end(p, kKNumLight);
     if (s || L.nitems == 0) return s;
     size_t smem = ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15) + sizeof(Acc) * kFusedRows +
                   sizeof(uint32_t) * (kFusedRows / 32) + sizeof(int) * (kFusedRows / 32 + 1);
@@ -821,10 +833,12 @@ static spg_status learned_kernels(spg_plan *p, LearnedState &L) {
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBatch, smem);
     if (occ < 1) occ = 1;
+    group_begin(p, kKNumHeavy);
     launch(p, kern, grid_for(L.nitems, 1, p->sm_count * occ), kBatch, smem, L.nitems, L.it_rec0, L.it_nrec, p->rec_col,
            p->rec_slab, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv, p->At_colptr, p->At_row,
            (const Acc *)p->At_val, p->split, p->T, p->R, L.capoff, L.cap, L.colfill, L.flag, L.nflag, L.item_cnt,
            L.item_pos, (OutIdx *)L.trow, (Acc *)L.tval, (unsigned long long *)(p->d_cnt + kCntFusedNextSlot));
+    group_end(p, kKNumHeavy);
     return cuda_check(cudaGetLastError(), "fused heavy");
 }
 
@@ -942,17 +956,17 @@ static spg_status learned_run(spg_plan *p, const spg_options *opt, spg_csc *C, i
     }
 
     // 3. the learned numeric work
-    group_begin(p, kKNumLight);
     spg_status s;
     if (p->acc_f64)
         s = p->out_idx64 ? learned_kernels<double, long long>(p, L) : learned_kernels<double, int>(p, L);
     else
         s = p->out_idx64 ? learned_kernels<long long, long long>(p, L) : learned_kernels<long long, int>(p, L);
-    group_end(p, kKNumLight);
     if (s) return s;
+    LTRY(cuda_check(cudaMemsetAsync(p->d_cnt + kCntNnzCHeavySlot, 0, sizeof(int64_t), st), "memset"));
     if (n > 0)
         launch(p, k_learned_nnz, grid_for(n, 256, sm * 8), 256, 0, n, p->bin_of, (const unsigned long long *)L.colfill,
-               (const int64_t *)L.nnz_light, (const int32_t *)L.flag, L.nnz);
+               (const int64_t *)L.nnz_light, (const int32_t *)L.flag, L.nnz,
+               (unsigned long long *)(p->d_cnt + kCntNnzCHeavySlot));
     LTRY(cuda_check(cudaMemcpyAsync(p->h_pinned + 18, L.nflag, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "nflag"));
     LTRY(cuda_check(cudaStreamSynchronize(st), "nflag"));
     const int64_t nf = p->h_pinned[18];
@@ -1025,6 +1039,8 @@ static spg_status learned_run(spg_plan *p, const spg_options *opt, spg_csc *C, i
     // 5. canonical column pointers, then C
     s = scan_exclusive_i64(p, L.nnz, p->Ccolptr, n);
     if (!s) s = cuda_check(cudaMemcpyAsync(p->h_pinned + 20, p->Ccolptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "nnz");
+    if (!s) s = cuda_check(cudaMemcpyAsync(p->h_pinned + 21, p->d_cnt + kCntNnzCHeavySlot, sizeof(int64_t),
+                                           cudaMemcpyDeviceToHost, st), "nnz");
     if (!s) s = cuda_check(cudaStreamSynchronize(st), "nnz");
     if (s) {
         if (sub) spgemm_plan_destroy(sub);
@@ -1032,6 +1048,7 @@ static spg_status learned_run(spg_plan *p, const spg_options *opt, spg_csc *C, i
     }
     p->nnzC = p->h_pinned[20];
     p->stats.nnzC = p->nnzC;
+    p->stats.nnzC_heavy = p->h_pinned[21];
     void *cp = alloc_out(opt, sizeof(int64_t) * (size_t)(n + 1));
     void *ri = alloc_out(opt, idxsz * (size_t)p->nnzC);
     void *va = alloc_out(opt, 8 * (size_t)p->nnzC);

@@ -104,6 +104,10 @@ def learned_vs_exact(A, B, model, slack, P=4, b=256, **kw):
                                   **kw)
     stats = g.spgemm_last_multiply_stats()
     torch.cuda.synchronize()
+    # the fused pass's output entries: none without heavy columns, never more than C
+    assert 0 <= stats["nnzC_heavy"] <= stats["nnzC"]
+    if stats["heavy_columns"] == 0:
+        assert stats["nnzC_heavy"] == 0
     assert torch.equal(Cl.colptr, Ce.colptr)
     assert torch.equal(Cl.rowidx, Ce.rowidx)
     if Cl.vals.dtype == torch.int64:
