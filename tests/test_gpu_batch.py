@@ -82,3 +82,23 @@ def test_autotuners_write_and_reuse_cache(tmp_path):
     C = g.multiply(dA, dA, P=4, b=256, light_max=pb["light_max"], slab_rows=pb["slab_rows"])
     ref = oracle.spgemm(A, A)
     assert np.array_equal(C.colptr.cpu().numpy(), ref["colptr"])
+
+
+@pytest.mark.slow
+def test_batch_full_range_instances():
+    """The first 48 of the benchmark's 512 instances (the generator draws them in
+    order from one seeded stream: n log-uniform in [1000, 200000], ER or R-MAT
+    rows, 4..32 per column, f64), with the benchmark's tuned task size: every
+    instance in full against the oracle."""
+    pairs = synth.batch_instances(48, 1000, 200000, seed=0)
+    As = [g.to_device(A, ptr_dtype=torch.int32, idx_dtype=torch.int32) for A, _ in pairs]
+    Bs = [g.to_device(B, ptr_dtype=torch.int32, idx_dtype=torch.int32) for _, B in pairs]
+    batch = g.spgemm_batch_create(As, Bs, task_cols=16, warps_per_cta=4)
+    g.spgemm_batch_execute(batch)
+    assert g.spgemm_batch_status(batch) == g.SPG_OK
+    for i, (A, B) in enumerate(pairs):
+        cp, ri, v = g.spgemm_batch_result(batch, i)
+        ref = oracle.spgemm(A, B)
+        assert np.array_equal(cp.cpu().numpy(), ref["colptr"]), i
+        assert np.array_equal(ri.cpu().numpy().astype(np.int64), ref["rowidx"]), i
+        check_values(v.cpu().numpy(), ref["vals"], ref["absum"], f"instance {i}")
