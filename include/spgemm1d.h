@@ -103,6 +103,21 @@ typedef struct {
     void *alloc_ctx;
     const void *model;      /* spg_model* for SPG_SIZING_LEARNED, else NULL */
     double learned_slack;   /* capacity = ceil(slack * predicted nnz) for learned sizing (0 = 1.25) */
+    /* Optional structural output mask (the masked product C<M> = A*B that the
+     * batched betweenness search of Section 3.2 multiplies with; NULL = none).
+     * Column j of C keeps row r iff bit (r & 31) of mask[j * mask_words +
+     * (r >> 5)] is set, inverted when mask_complement = 1.  An entry of A*B
+     * outside the mask is neither counted nor stored; entries inside it are
+     * exactly those of A*B.  Device memory of n * mask_words words owned by the
+     * caller; the symbolic and numeric passes (and a refresh or graph replay of
+     * the plan) read it, so it must stay valid and unchanged until the plan is
+     * destroyed.  Not available with learned sizing, spgemm_outer_multiply or
+     * spgemm_bc_batch (which masks its own products): those return
+     * SPG_INVALID_ARGUMENT. */
+    const uint32_t *mask;
+    int64_t mask_words;     /* words per column of mask, >= ceil(nrows(A) / 32) */
+    int32_t mask_complement; /* 0: keep rows whose bit is set; 1: keep rows whose bit is clear */
+    int32_t reserved2;
 } spg_options;
 
 /* Counters of one plan (filled progressively by plan, symbolic and numeric). */

@@ -33,6 +33,10 @@ Functions and the passages they follow:
 * ``outer_volumes`` -- what Algorithm 3 moves between P owners: B entries that
                        change owner, partial-product nonzeros, and partial
                        nonzeros computed away from their column's owner.
+* ``spgemm_masked`` -- C<M> = A*B with a structural mask (the masked product
+                       of the batched betweenness search, Section 3.2): the
+                       entries of A*B whose position M's pattern holds (or,
+                       complemented, does not hold).
 """
 from __future__ import annotations
 
@@ -154,6 +158,29 @@ def spgemm(A, B, cols=None, nthreads: int = 0):
         raise RuntimeError(f"orc_fill failed ({rc})")
     return {"colptr": colptr, "rowidx": rowidx, "vals": vals, "absum": absum,
             "nnz": nnz, "flops": flops, "nrows": A.nrows, "ncols": ns}
+
+
+def spgemm_masked(A, B, M, complement: bool = False, cols=None):
+    """C<M> = A * B(:, cols) under the structural mask M (a CSC pattern with
+    C's shape; values ignored): by definition the unmasked product, then, per
+    column j, only the entries whose row r satisfies (r in M(:, j)) != complement.
+    Same return layout as ``spgemm``."""
+    r = spgemm(A, B, cols=cols)
+    cols = np.arange(B.ncols, dtype=np.int64) if cols is None else np.asarray(cols, dtype=np.int64)
+    mcp = np.asarray(M.colptr, dtype=np.int64)
+    mri = np.asarray(M.rowidx, dtype=np.int64)
+    keep = np.zeros(r["rowidx"].shape[0], dtype=bool)
+    for s, j in enumerate(cols):
+        a, e = int(r["colptr"][s]), int(r["colptr"][s + 1])
+        inside = np.isin(r["rowidx"][a:e], mri[mcp[j]:mcp[j + 1]])
+        keep[a:e] = inside != bool(complement)
+    nnz = np.array([int(keep[r["colptr"][s]:r["colptr"][s + 1]].sum()) for s in range(cols.shape[0])],
+                   dtype=np.int64)
+    colptr = np.zeros(cols.shape[0] + 1, dtype=np.int64)
+    np.cumsum(nnz, out=colptr[1:])
+    return {"colptr": colptr, "rowidx": r["rowidx"][keep], "vals": r["vals"][keep],
+            "absum": None if r["absum"] is None else r["absum"][keep], "nnz": nnz, "flops": r["flops"],
+            "nrows": r["nrows"], "ncols": r["ncols"]}
 
 
 def plan_block(A, B, c0: int, c1: int, b: int):

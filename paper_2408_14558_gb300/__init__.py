@@ -58,7 +58,8 @@ class spg_options(ctypes.Structure):
                 ("slab_rows", ctypes.c_int32), ("split", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p), ("model", ctypes.c_void_p),
-                ("learned_slack", ctypes.c_double)]
+                ("learned_slack", ctypes.c_double), ("mask", ctypes.c_void_p), ("mask_words", ctypes.c_int64),
+                ("mask_complement", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class spg_stats(ctypes.Structure):
@@ -195,8 +196,23 @@ class _TorchAllocator:
             torch.empty(0, dtype=dtype, device=self.device)
 
 
+def _mask_fields(mask, nrows, ncols):
+    """(pointer, words per column) of an output mask: a CUDA int32 tensor of
+    shape (ncols of C, words >= ceil(nrows / 32)), row-major, bit r of row j's
+    words = row r of column j (least significant bit first)."""
+    if mask is None:
+        return None, 0
+    if mask.dtype != torch.int32 or mask.dim() != 2 or not mask.is_cuda or not mask.is_contiguous():
+        raise ValueError("mask must be a contiguous 2-D CUDA int32 tensor (columns x words)")
+    if mask.shape[1] < (nrows + 31) // 32 or mask.shape[0] < ncols:
+        raise ValueError(f"mask needs {ncols} columns of >= {(nrows + 31) // 32} words, has shape "
+                         f"{tuple(mask.shape)}")
+    return mask.data_ptr(), int(mask.shape[1])
+
+
 def make_options(P=1, b=1024, stream=None, validate=True, light_max=0, slab_rows=0, sizing=SPG_SIZING_EXACT,
-                 model=None, learned_slack=0.0, allocator=None, split=0) -> spg_options:
+                 model=None, learned_slack=0.0, allocator=None, split=0, mask=None, mask_words=0,
+                 mask_complement=False) -> spg_options:
     lib = load_library()
     o = spg_options()
     lib.spgemm_default_options(ctypes.byref(o))
@@ -210,6 +226,8 @@ def make_options(P=1, b=1024, stream=None, validate=True, light_max=0, slab_rows
     o.model = model
     if learned_slack:
         o.learned_slack = float(learned_slack)
+    if mask is not None:
+        o.mask, o.mask_words, o.mask_complement = mask, int(mask_words), 1 if mask_complement else 0
     return o
 
 
@@ -236,15 +254,22 @@ class Plan:
 
 
 def spgemm_plan(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, validate=True, light_max=0,
-                slab_rows=0, split=0) -> Plan:
-    """Steps 1-4 of Algorithm 1; split = SPG_SPLIT_UNIFORM or SPG_SPLIT_FLOPS."""
+                slab_rows=0, split=0, mask=None, mask_complement=False) -> Plan:
+    """Steps 1-4 of Algorithm 1; split = SPG_SPLIT_UNIFORM or SPG_SPLIT_FLOPS;
+    mask = an optional output mask (a CUDA int32 tensor, columns x words, bit
+    r of column j's words = row r), kept alive with the plan; mask_complement
+    keeps the rows whose bit is clear."""
     lib = load_library()
     alloc = _TorchAllocator(A.colptr.device)
-    opts = make_options(P, b, stream, validate, light_max, slab_rows, allocator=alloc, split=split)
+    mp, mw = _mask_fields(mask, A.nrows, B.ncols)
+    opts = make_options(P, b, stream, validate, light_max, slab_rows, allocator=alloc, split=split, mask=mp,
+                        mask_words=mw, mask_complement=mask_complement)
     a, bb = A.as_c(), B.as_c()
     h = ctypes.c_void_p()
     _check(lib.spgemm_plan(ctypes.byref(a), ctypes.byref(bb), ctypes.byref(opts), ctypes.byref(h)))
-    return Plan(h, A, B, opts, alloc)
+    plan = Plan(h, A, B, opts, alloc)
+    plan._mask = mask  # the plan's passes read it
+    return plan
 
 
 def spgemm_symbolic(plan: Plan):
@@ -322,13 +347,16 @@ def spgemm_plan_destroy(plan: Plan):
 
 
 def spgemm_1d_multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, validate=True, light_max=0,
-                       slab_rows=0, sizing=SPG_SIZING_EXACT, model=None, learned_slack=0.0, split=0):
+                       slab_rows=0, sizing=SPG_SIZING_EXACT, model=None, learned_slack=0.0, split=0, mask=None,
+                       mask_complement=False):
     """plan + symbolic + numeric + destroy in one C call; C's arrays come from
     torch's allocator through the callbacks.  Returns (C, status)."""
     lib = load_library()
     alloc = _TorchAllocator(A.colptr.device)
+    mp, mw = _mask_fields(mask, A.nrows, B.ncols)
     opts = make_options(P, b, stream, validate, light_max, slab_rows, sizing,
-                        model.handle if model is not None else None, learned_slack, allocator=alloc, split=split)
+                        model.handle if model is not None else None, learned_slack, allocator=alloc, split=split,
+                        mask=mp, mask_words=mw, mask_complement=mask_complement)
     a, bb, c = A.as_c(), B.as_c(), spg_csc()
     st = _check(lib.spgemm_1d_multiply(ctypes.byref(a), ctypes.byref(bb), ctypes.byref(opts), ctypes.byref(c)))
     idx_dt = torch.int64 if c.idx_type == SPG_IDX_I64 else torch.int32

@@ -2,13 +2,17 @@
 // SpGEMM inside both phases, for one batch of s sources on an unweighted
 // graph A (n x n; column v lists the neighbours of v, values ignored).
 //   forward search  F_0 holds one entry per source (its own vertex, sigma 1);
-//                   F_{d+1} = (A * F_d) without the (vertex, source) pairs
-//                   already visited: its values are the shortest-path counts
-//                   sigma of the newly reached pairs (k_bc_count, a scan,
-//                   k_bc_keep, k_bc_mark on a visited bitmap of s x n bits)
-//   backward sweep  W_d = (1 + delta_d) / sigma_d on F_d's pattern, T = A * W_d,
-//                   delta_{d-1} = T on F_{d-1}'s pattern times sigma_{d-1}
-//                   (k_bc_weights, k_bc_delta), added into bc for d - 1 >= 1
+//                   F_{d+1} = A * F_d masked by the complement of the visited
+//                   bitmap (s x n bits): its values are the shortest-path
+//                   counts sigma of the newly reached (vertex, source) pairs;
+//                   k_bc_mark then adds them to the visited bitmap
+//   backward sweep  W_d = (1 + delta_d) / sigma_d on F_d's pattern,
+//                   T = A * W_d masked by F_{d-1}'s pattern (a bitmap built by
+//                   k_bc_mark), delta_{d-1} = T times sigma_{d-1} on F_{d-1}'s
+//                   entries (k_bc_weights, k_bc_delta), added into bc for
+//                   d - 1 >= 1
+// Both masks are applied inside the SpGEMM (symbolic and numeric passes), so
+// no product outside them is counted or stored.
 // A frontier column j belongs to source j; row v of it is vertex v.
 #include <algorithm>
 #include <vector>
@@ -45,49 +49,6 @@ __global__ void k_bc_init(const int32_t *src, int s, int64_t W, int64_t *colptr,
     }
 }
 
-__device__ __forceinline__ bool bc_visited(const uint32_t *V, int64_t W, int64_t j, int64_t r) {
-    return (V[j * W + (r >> 5)] >> (r & 31)) & 1u;
-}
-
-// Entries of T(:, j) whose (vertex, source) pair is not visited yet.
-__global__ void k_bc_count(const int64_t *Tcp, const void *Trow, int i64, int64_t s, const uint32_t *V, int64_t W,
-                           int64_t *cnt) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < s;
-         j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        int64_t c = 0;
-        for (int64_t e = Tcp[j] + lane; e < Tcp[j + 1]; e += 32) c += !bc_visited(V, W, j, ld_ptr(Trow, i64, e));
-        c = warp_sum_ll(c);
-        if (lane == 0) cnt[j] = c;
-    }
-}
-
-// The unvisited entries of T(:, j), in row order, into F(:, j).
-__global__ void k_bc_keep(const int64_t *Tcp, const void *Trow, const double *Tval, int i64, int64_t s,
-                          const uint32_t *V, int64_t W, const int64_t *Fcp, void *Frow, double *Fval) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < s;
-         j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        int64_t out = Fcp[j];
-        for (int64_t e0 = Tcp[j]; e0 < Tcp[j + 1]; e0 += 32) {
-            const int64_t e = e0 + lane;
-            const bool in = e < Tcp[j + 1];
-            const int64_t r = in ? ld_ptr(Trow, i64, e) : 0;
-            const bool keep = in && !bc_visited(V, W, j, r);
-            const uint32_t m = __ballot_sync(kFull, keep);
-            if (keep) {
-                const int64_t o = out + __popc(m & ((1u << lane) - 1u));
-                if (i64)
-                    ((int64_t *)Frow)[o] = r;
-                else
-                    ((int32_t *)Frow)[o] = (int32_t)r;
-                Fval[o] = Tval[e];
-            }
-            out += __popc(m);
-        }
-    }
-}
-
 __global__ void k_bc_mark(const int64_t *Fcp, const void *Frow, int i64, int64_t s, uint32_t *V, int64_t W) {
     const int lane = threadIdx.x & 31;
     for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < s;
@@ -103,8 +64,9 @@ __global__ void k_bc_weights(const double *sigma, const double *delta, int64_t n
         w[i] = (1.0 + (delta ? delta[i] : 0.0)) / sigma[i];
 }
 
-// delta(v, j) = T(v, j) * sigma(v, j) over F(:, j)'s entries (T's column is
-// searched for row v); added into bc[v] when `add`.
+// delta(v, j) = T(v, j) * sigma(v, j) over F(:, j)'s entries (T's column,
+// whose rows are a subset of F's, is searched for row v); added into bc[v]
+// when `add`.
 __global__ void k_bc_delta(const int64_t *Fcp, const void *Frow, const double *Fsig, const int64_t *Tcp,
                            const void *Trow, const double *Tval, int i64, int64_t s, double *delta, double *bc,
                            int add) {
@@ -185,6 +147,10 @@ extern "C" spg_status spgemm_bc_batch(const spg_csc *A, const int32_t *sources, 
         set_error("A, options, bc and (for s > 0) sources must not be NULL; s >= 0");
         return SPG_INVALID_ARGUMENT;
     }
+    if (opt->mask) {
+        set_error("betweenness masks its own products: pass options without a mask");
+        return SPG_INVALID_ARGUMENT;
+    }
     if (A->nrows != A->ncols || !A->colptr) {
         set_error("betweenness needs a square adjacency matrix (got %lld x %lld)", (long long)A->nrows,
                   (long long)A->ncols);
@@ -223,10 +189,10 @@ extern "C" spg_status spgemm_bc_batch(const spg_csc *A, const int32_t *sources, 
         G.val_type = SPG_VAL_F64;
         G.vals = ws_alloc(w, sizeof(double) * (size_t)std::max<int64_t>(A->nnz, 1));
         uint32_t *V = (uint32_t *)ws_alloc(w, sizeof(uint32_t) * (size_t)(s * W + 1));
-        int64_t *cnt = (int64_t *)ws_alloc(w, sizeof(int64_t) * (size_t)(s + 1));
+        uint32_t *Mb = (uint32_t *)ws_alloc(w, sizeof(uint32_t) * (size_t)(s * W + 1));
         int *derr = (int *)ws_alloc(w, sizeof(int));
         int64_t *hn = nullptr;
-        if (!G.vals || !V || !cnt || !derr) BC_TRY(SPG_OUT_OF_MEMORY);
+        if (!G.vals || !V || !Mb || !derr) BC_TRY(SPG_OUT_OF_MEMORY);
         BC_TRY(cuda_check(cudaMallocHost(&hn, sizeof(int64_t) * 2), "cudaMallocHost"));
         BC_TRY(cuda_check(cudaMemsetAsync(V, 0, sizeof(uint32_t) * (size_t)(s * W + 1), st), "memset"));
         BC_TRY(cuda_check(cudaMemsetAsync(derr, 0, sizeof(int), st), "memset"));
@@ -255,50 +221,24 @@ extern "C" spg_status spgemm_bc_batch(const spg_csc *A, const int32_t *sources, 
         }
         S.frontier_nnz = s;
         // forward search
-        while (true) {
-            spg_csc T{};
-            BC_TRY(multiply_f64(&G, &run.F.back(), opt, &T, &S.products_forward));
-            launch(w, k_bc_count, grid_for(s * 32, 256, sm * 16), 256, 0, (const int64_t *)T.colptr, T.rowidx, i64,
-                   (int64_t)s, V, W, cnt);
-            spg_csc N{};
-            N.nrows = n;
-            N.ncols = s;
-            N.ptr_type = SPG_IDX_I64;
-            N.idx_type = A->idx_type;
-            N.val_type = SPG_VAL_F64;
-            N.colptr = alloc_user(opt, sizeof(int64_t) * (size_t)(s + 1));
-            rc = N.colptr ? scan_exclusive_i64(w, cnt, (int64_t *)N.colptr, s) : SPG_OUT_OF_MEMORY;
-            if (!rc) rc = cuda_check(cudaMemcpyAsync(hn, (int64_t *)N.colptr + s, sizeof(int64_t),
-                                                     cudaMemcpyDeviceToHost, st), "frontier");
-            if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "frontier");
-            if (rc) {
-                run.free_csc(T);
-                run.free_csc(N);
-                goto done;
+        {
+            spg_options fo = *opt;
+            fo.mask = V;
+            fo.mask_words = W;
+            fo.mask_complement = 1;
+            while (true) {
+                spg_csc T{};
+                BC_TRY(multiply_f64(&G, &run.F.back(), &fo, &T, &S.products_forward));
+                if (T.nnz == 0) {
+                    run.free_csc(T);
+                    break;
+                }
+                launch(w, k_bc_mark, grid_for(s * 32, 256, sm * 16), 256, 0, (const int64_t *)T.colptr, T.rowidx,
+                       i64, (int64_t)s, V, W);
+                run.F.push_back(T);
+                BC_TRY(cuda_check(cudaGetLastError(), "frontier kernels"));
+                S.frontier_nnz += T.nnz;
             }
-            N.nnz = *hn;
-            if (N.nnz == 0) {
-                run.free_csc(T);
-                run.free_csc(N);
-                break;
-            }
-            N.rowidx = alloc_user(opt, ib * (size_t)N.nnz);
-            N.vals = alloc_user(opt, 8 * (size_t)N.nnz);
-            if (!N.rowidx || !N.vals) {
-                run.free_csc(T);
-                run.free_csc(N);
-                BC_TRY(SPG_OUT_OF_MEMORY);
-            }
-            launch(w, k_bc_keep, grid_for(s * 32, 256, sm * 16), 256, 0, (const int64_t *)T.colptr, T.rowidx,
-                   (const double *)T.vals, i64, (int64_t)s, V, W, (const int64_t *)N.colptr, N.rowidx,
-                   (double *)N.vals);
-            launch(w, k_bc_mark, grid_for(s * 32, 256, sm * 16), 256, 0, (const int64_t *)N.colptr, N.rowidx, i64,
-                   (int64_t)s, V, W);
-            rc = cuda_check(cudaGetLastError(), "frontier kernels");
-            run.free_csc(T);
-            run.F.push_back(N);
-            if (rc) goto done;
-            S.frontier_nnz += N.nnz;
         }
         cudaEventRecord(ev[1], st);
         S.levels = (int64_t)run.F.size();
@@ -310,9 +250,16 @@ extern "C" spg_status spgemm_bc_batch(const spg_csc *A, const int32_t *sources, 
             if (!Wd.vals) BC_TRY(SPG_OUT_OF_MEMORY);
             launch(w, k_bc_weights, grid_for(Wd.nnz, 256, sm * 8), 256, 0, (const double *)run.F[d].vals,
                    (const double *)run.delta[d], Wd.nnz, (double *)Wd.vals);
-            spg_csc T{};
-            BC_TRY(multiply_f64(&G, &Wd, opt, &T, &S.products_backward));
             const spg_csc &Fp = run.F[d - 1];
+            BC_TRY(cuda_check(cudaMemsetAsync(Mb, 0, sizeof(uint32_t) * (size_t)(s * W + 1), st), "memset"));
+            launch(w, k_bc_mark, grid_for(s * 32, 256, sm * 16), 256, 0, (const int64_t *)Fp.colptr, Fp.rowidx, i64,
+                   (int64_t)s, Mb, W);
+            spg_options bo = *opt;
+            bo.mask = Mb;
+            bo.mask_words = W;
+            bo.mask_complement = 0;
+            spg_csc T{};
+            BC_TRY(multiply_f64(&G, &Wd, &bo, &T, &S.products_backward));
             run.delta[d - 1] = (double *)alloc_user(opt, 8 * (size_t)std::max<int64_t>(Fp.nnz, 1));
             if (!run.delta[d - 1]) {
                 run.free_csc(T);

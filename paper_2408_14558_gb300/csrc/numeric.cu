@@ -19,7 +19,8 @@ __global__ void __launch_bounds__(WARPS * 32)
     k_num_light(const int32_t *__restrict__ list, int64_t ncols, const void *Bcolptr, int p64,
                 const int32_t *__restrict__ Bq, const Acc *__restrict__ Bv, const int64_t *__restrict__ At_colptr,
                 const int32_t *__restrict__ At_row, const Acc *__restrict__ At_val,
-                const int64_t *__restrict__ Ccolptr, OutIdx *__restrict__ Crow, Acc *__restrict__ Cval, int *err) {
+                const int64_t *__restrict__ Ccolptr, OutIdx *__restrict__ Crow, Acc *__restrict__ Cval, int *err,
+                OutMask mask) {
     constexpr int S = 1 << LOGS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSeg<Acc> *segs = (WarpSeg<Acc> *)smem_raw;
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                 }
             },
             [&](int r, Acc v) {
+                if (mask.bits && !mask_keeps(mask, j, r)) return;
                 bool fresh;
                 int slot = hash_insert(keys, LOGS, r, &fresh);
                 if (slot < 0)
@@ -124,8 +126,9 @@ __global__ void k_num_headers(int64_t nitems, const int32_t *__restrict__ num_re
 // the lower bits); products accumulate at acc[rank]; the item is then written
 // at its final place in C, values and rows each as one coalesced run.  Thread
 // 0 claims the next item when the current one starts and fetches its header
-// while the current one is written out.
-template <typename Acc, typename OutIdx>
+// while the current one is written out.  MASKED: the bitmaps hold only the
+// rows an output mask admits, and a product whose row is absent is dropped.
+template <typename Acc, typename OutIdx, bool MASKED>
 __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
     k_num_heavy(int64_t nitems, const NumItem *__restrict__ items, const uint32_t *__restrict__ hbits,
                 const int32_t *__restrict__ Bq, const Acc *__restrict__ Bv, const int64_t *__restrict__ At_colptr,
@@ -188,12 +191,16 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
                     // a row missing from the symbolic bitmap (never expected) goes
                     // to the dump slot acc[cap] and is reported
                     const bool hit = (x.x >> sh) & 1u;
-                    miss |= !hit;
+                    miss |= !hit && !MASKED;  // a masked product is absent by design
                     atomic_add_acc(acc + (hit ? (int)(x.y + __popc(x.x & ((1u << sh) - 1u))) : cap), v);
 #else
-                    // the rank of a present row; an absent one would still land
-                    // inside [0, cnt] (never outside the accumulator)
-                    atomic_add_acc(acc + (int)(x.y + __popc(x.x & ((1u << sh) - 1u))), v);
+                    if constexpr (MASKED) {
+                        if ((x.x >> sh) & 1u) atomic_add_acc(acc + (int)(x.y + __popc(x.x & ((1u << sh) - 1u))), v);
+                    } else {
+                        // the rank of a present row; an absent one would still
+                        // land inside [0, cnt] (never outside the accumulator)
+                        atomic_add_acc(acc + (int)(x.y + __popc(x.x & ((1u << sh) - 1u))), v);
+                    }
 #endif
                 });
             if (miss) bad_sh = 1;
@@ -265,7 +272,7 @@ static spg_status launch_num_light(spg_plan *p, const int32_t *list, int64_t cnt
     int g = grid_for(cnt, WARPS, p->sm_count * occ);
     launch(p, kern, g, WARPS * 32, smem, list, cnt, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq,
                                          (const Acc *)p->Bv, p->At_colptr, p->At_row, (const Acc *)p->At_val,
-                                         p->Ccolptr, (OutIdx *)C->rowidx, (Acc *)C->vals, p->d_err);
+                                         p->Ccolptr, (OutIdx *)C->rowidx, (Acc *)C->vals, p->d_err, p->omask);
     return cuda_check(cudaGetLastError(), "numeric light");
 }
 
@@ -293,7 +300,7 @@ static spg_status numeric_typed(spg_plan *p, spg_csc *C) {
         const int threads = kBatch;
         size_t smem = ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15) + sizeof(Acc) * (size_t)(p->num_cap + 1) +
                       sizeof(uint2) * (size_t)kNumMaxWords;
-        auto kern = k_num_heavy<Acc, OutIdx>;
+        auto kern = p->omask.bits ? k_num_heavy<Acc, OutIdx, true> : k_num_heavy<Acc, OutIdx, false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int occ = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);

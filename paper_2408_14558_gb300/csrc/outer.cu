@@ -184,6 +184,10 @@ extern "C" spg_status spgemm_outer_multiply(const spg_csc *A, const spg_csc *B, 
                   (long long)A->nrows, (long long)A->ncols, (long long)B->nrows, (long long)B->ncols, opt->P);
         return SPG_INVALID_ARGUMENT;
     }
+    if (opt->mask) {
+        set_error("an output mask is not available with the outer-product form");
+        return SPG_INVALID_ARGUMENT;
+    }
     const int P = opt->P;
     const int64_t k = B->nrows, n = B->ncols, Pn = (int64_t)P * n;
     const bool a_idx64 = A->idx_type == SPG_IDX_I64;

@@ -1087,6 +1087,17 @@ extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_
         set_error("light_max must be a power of two in [32, 1024] and slab_rows one in [1024, 16384]");
         return SPG_INVALID_ARGUMENT;
     }
+    if (opt->mask) {
+        if (opt->mask_words < (A->nrows + 31) / 32 || (opt->mask_complement != 0 && opt->mask_complement != 1)) {
+            set_error("mask_words must be >= ceil(nrows(A) / 32) = %lld and mask_complement 0 or 1",
+                      (long long)((A->nrows + 31) / 32));
+            return SPG_INVALID_ARGUMENT;
+        }
+        if (opt->sizing == SPG_SIZING_LEARNED) {
+            set_error("an output mask is not available with learned sizing");
+            return SPG_INVALID_ARGUMENT;
+        }
+    }
 
     spg_plan *p = new (std::nothrow) spg_plan();
     if (!p) {
@@ -1096,6 +1107,11 @@ extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_
     p->A = *A;
     p->B = *B;
     p->opt = *opt;
+    if (opt->mask) {
+        p->omask.bits = opt->mask;
+        p->omask.words = opt->mask_words;
+        p->omask.flip = opt->mask_complement ? ~0u : 0u;
+    }
     p->st = (cudaStream_t)opt->stream;
     p->m = A->nrows;
     p->k = A->ncols;

@@ -52,9 +52,21 @@ struct Alloc {
 
 }  // namespace spg
 
+// Optional output mask of a plan: column j of C keeps row r iff bit r of
+// column j's words, XOR flip, is set (flip = ~0 for a complemented mask).
+struct OutMask {
+    const uint32_t *bits = nullptr;  // nullptr: every row is kept
+    int64_t words = 0;               // words per column
+    uint32_t flip = 0;
+};
+__device__ __forceinline__ bool mask_keeps(const OutMask &m, int64_t j, int r) {
+    return ((__ldg(m.bits + j * m.words + (r >> 5)) ^ m.flip) >> (r & 31)) & 1u;
+}
+
 struct spg_plan {
     spg_csc A{}, B{};
     spg_options opt{};
+    OutMask omask;
     cudaStream_t st = nullptr;
     int64_t m = 0, k = 0, n = 0, nnzA = 0, nnzB = 0;
     int P = 1;

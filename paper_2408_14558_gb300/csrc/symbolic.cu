@@ -15,7 +15,7 @@ template <int LOGS, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
     k_sym_light(const int32_t *__restrict__ list, int64_t ncols, const void *Bcolptr, int p64,
                 const int32_t *__restrict__ Bq, const int64_t *__restrict__ At_colptr,
-                const int32_t *__restrict__ At_row, int64_t *__restrict__ nnzcol, int *err) {
+                const int32_t *__restrict__ At_row, int64_t *__restrict__ nnzcol, int *err, OutMask mask) {
     constexpr int S = 1 << LOGS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSeg<long long> *segs = (WarpSeg<long long> *)smem_raw;
@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                 }
             },
             [&](int r, long long) {
+                if (mask.bits && !mask_keeps(mask, j, r)) return;
                 bool fresh;
                 if (hash_insert(tab, LOGS, r, &fresh) < 0) full = true;
                 cnt += fresh ? 1 : 0;
@@ -60,7 +61,7 @@ __global__ void SPG_SYM_BOUNDS
                 const int32_t *__restrict__ At_row, const int32_t *__restrict__ split, int T, int R,
                 uint32_t *__restrict__ hbits, int32_t *__restrict__ rec_cnt, unsigned long long *next,
                 const int64_t *__restrict__ flops, const int32_t *__restrict__ win_lo,
-                const int32_t *__restrict__ win_hi) {
+                const int32_t *__restrict__ win_hi, OutMask mask, int64_t mwords_used) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RW = R >> 5;
     CtaBatch<long long> &sb = *(CtaBatch<long long> *)smem_raw;
@@ -97,6 +98,14 @@ __global__ void SPG_SYM_BOUNDS
                     atomicOr(bits + ((r >> 5) - wbase), 1u << (r & 31));
             });
         // cta_products ends with a barrier: the bitmap is complete
+        if (mask.bits) {
+            // keep the rows the output mask admits (words past the last row of
+            // C hold no products and have no mask words)
+            const uint32_t *mw = mask.bits + (int64_t)j * mask.words;
+            for (int w = threadIdx.x; w < nwords; w += blockDim.x)
+                bits[w] = wbase + w < mwords_used ? bits[w] & (__ldg(mw + wbase + w) ^ mask.flip) : 0u;
+            __syncthreads();
+        }
         uint32_t *dst = hbits + (int64_t)r0 * RW;
         for (int w = threadIdx.x; w < nwords; w += blockDim.x) st_stream(dst + w, bits[w]);
         for (int rr = wid; rr < nr; rr += nw) {
@@ -176,7 +185,7 @@ static spg_status launch_sym_light(spg_plan *p, const int32_t *list, int64_t cnt
     if (occ < 1) occ = 1;
     int g = grid_for(cnt, WARPS, p->sm_count * occ);
     launch(p, kern, g, WARPS * 32, smem, list, cnt, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr,
-           p->At_row, p->nnzcol, p->d_err);
+           p->At_row, p->nnzcol, p->d_err, p->omask);
     return cuda_check(cudaGetLastError(), "symbolic light");
 }
 
@@ -195,7 +204,7 @@ static spg_status symbolic_heavy(spg_plan *p) {
     launch(p, k_sym_heavy, g, threads, smem, p->nsym, p->sym_rec0, p->sym_nrec, p->rec_col, p->rec_slab,
            p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr, p->At_row, p->split, p->T, p->R,
            p->hbits, p->rec_cnt, (unsigned long long *)(p->d_cnt + kCntSymNextSlot), p->flops, p->win_lo,
-           p->win_hi);
+           p->win_hi, p->omask, (int64_t)((p->m + 31) / 32));
     group_end(p, kKSymHeavy);
     int64_t *nnum = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
     int64_t *num_first = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));

@@ -51,3 +51,16 @@ def run_gpu(A, B, P, b, ptr=torch.int32, idx=torch.int32, val=None, **kw):
     C = g.multiply(dA, dB, P, b, **kw)
     torch.cuda.synchronize()
     return C
+
+
+def mask_from_pattern(M, device="cuda", words=None):
+    """Output-mask tensor (columns x words int32, bit r of column j's words =
+    row r, least significant bit first) whose set bits are the host CSC M's
+    pattern."""
+    cp = np.asarray(M.colptr, dtype=np.int64)
+    ri = np.asarray(M.rowidx, dtype=np.int64)
+    W = (int(M.nrows) + 31) // 32 if words is None else int(words)
+    bits = np.zeros((int(M.ncols), W), dtype=np.uint32)
+    cols = np.repeat(np.arange(int(M.ncols), dtype=np.int64), np.diff(cp))
+    np.bitwise_or.at(bits, (cols, ri >> 5), np.left_shift(np.uint32(1), (ri & 31).astype(np.uint32)))
+    return torch.from_numpy(bits.view(np.int32)).to(device)

@@ -50,6 +50,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", offsetof(spg_csc, colptr), offsetof(spg_options, stream),
          offsetof(spg_options, learned_slack), offsetof(spg_stats, ms_plan));
   printf("%zu %zu\\n", sizeof(spg_outer_stats), offsetof(spg_outer_stats, ms_split));
+  printf("%zu %zu\\n", offsetof(spg_options, mask), offsetof(spg_options, mask_complement));
   return 0;
 }
 """)
@@ -66,6 +67,8 @@ int main(void) {
     assert sizes[6] == g.spg_stats.ms_plan.offset
     assert sizes[7] == ctypes.sizeof(g.spg_outer_stats)
     assert sizes[8] == g.spg_outer_stats.ms_split.offset
+    assert sizes[9] == g.spg_options.mask.offset
+    assert sizes[10] == g.spg_options.mask_complement.offset
 
 
 def test_default_options(lib):
@@ -140,3 +143,45 @@ def test_bc_argument_errors_need_no_gpu(lib):
     assert f(ctypes.byref(A), None, 0, ctypes.byref(o), ctypes.addressof(fake), None, 0, None) == g.SPG_INVALID_ARGUMENT
     A.nrows = 5
     assert f(ctypes.byref(A), None, 3, ctypes.byref(o), ctypes.addressof(fake), None, 0, None) == g.SPG_INVALID_ARGUMENT
+
+
+def test_mask_argument_errors_need_no_gpu(lib):
+    """A mask with too few words per column, a complement flag other than
+    0 / 1, or a mask with learned sizing, the outer-product form or the
+    betweenness batch is rejected before any CUDA call."""
+    import paper_2408_14558_gb300 as g
+    A = g.spg_csc(70, 5, 0, 0, 0, 0, 0, 1, None, None)
+    B = g.spg_csc(5, 3, 0, 0, 0, 0, 0, 1, None, None)
+    words = (ctypes.c_uint32 * 16)()
+    o = g.spg_options()
+    lib.spgemm_default_options(ctypes.byref(o))
+    assert o.mask is None and o.mask_words == 0 and o.mask_complement == 0
+    o.mask = ctypes.addressof(words)
+    o.mask_words = 2                         # 70 rows need 3 words
+    h = ctypes.c_void_p()
+    assert lib.spgemm_plan(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(h)) == g.SPG_INVALID_ARGUMENT
+    assert "mask_words" in g.spgemm_last_error()
+    o.mask_words = 3
+    o.mask_complement = 2
+    assert lib.spgemm_plan(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(h)) == g.SPG_INVALID_ARGUMENT
+    o.mask_complement = 1
+    o.sizing = g.SPG_SIZING_LEARNED
+    assert lib.spgemm_plan(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(h)) == g.SPG_INVALID_ARGUMENT
+    assert "learned" in g.spgemm_last_error()
+    assert not h.value
+    o.sizing = g.SPG_SIZING_EXACT
+    C = g.spg_csc()
+    f = lib.spgemm_outer_multiply
+    f.argtypes = [ctypes.POINTER(g.spg_csc), ctypes.POINTER(g.spg_csc), ctypes.POINTER(g.spg_options),
+                  ctypes.POINTER(g.spg_csc), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    assert f(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(C), None) == g.SPG_INVALID_ARGUMENT
+    assert "outer" in g.spgemm_last_error()
+    fb = lib.spgemm_bc_batch
+    fb.argtypes = [ctypes.POINTER(g.spg_csc), ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(g.spg_options),
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    fb.restype = ctypes.c_int
+    G = g.spg_csc(5, 5, 0, 0, 0, 0, 0, 1, None, None)
+    fake = ctypes.c_double(0.0)
+    assert fb(ctypes.byref(G), None, 0, ctypes.byref(o), ctypes.addressof(fake), None, 0, None) == g.SPG_INVALID_ARGUMENT
+    assert "mask" in g.spgemm_last_error()

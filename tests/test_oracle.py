@@ -546,3 +546,90 @@ def test_bc_matches_networkx_subset():
     G.add_edges_from(edges)
     ref = nx.betweenness_centrality_subset(G, src, list(range(n)), normalized=False)
     assert np.allclose(bc, 2 * np.array([ref[v] for v in range(n)]))
+
+
+# ------------------------------------------------------------- masked product
+
+def _dense_pattern(M):
+    P = np.zeros((M.nrows, M.ncols), dtype=bool)
+    for j in range(M.ncols):
+        P[np.asarray(M.rowidx[M.colptr[j]:M.colptr[j + 1]], dtype=np.int64), j] = True
+    return P
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("complement", [False, True])
+def test_masked_product_equals_dense_masked_matmul(seed, complement):
+    """C<M> against dense arithmetic: small integers (exact in doubles), the
+    structure from the boolean product of the patterns, masked entry by entry."""
+    rng = np.random.default_rng(seed)
+    A = synth.random_sparse(23, 17, 0.2, rng, values="small")
+    B = synth.random_sparse(17, 11, 0.25, rng, values="small")
+    M = synth.random_sparse(23, 11, 0.4, rng, values="f64")
+    C = oracle.spgemm_masked(A, B, M, complement=complement)
+    assert_sorted_unique(C)
+    Da = np.zeros((23, 17))
+    Db = np.zeros((17, 11))
+    for j in range(17):
+        Da[A.rowidx[A.colptr[j]:A.colptr[j + 1]], j] = A.vals[A.colptr[j]:A.colptr[j + 1]]
+    for j in range(11):
+        Db[B.rowidx[B.colptr[j]:B.colptr[j + 1]], j] = B.vals[B.colptr[j]:B.colptr[j + 1]]
+    struct = (_dense_pattern(A).astype(int) @ _dense_pattern(B).astype(int)) > 0
+    keep = struct & (_dense_pattern(M) != complement)
+    assert np.array_equal(pattern_dense(C), keep)
+    assert np.array_equal(to_dense(C)[keep], (Da @ Db)[keep])
+
+
+def test_masked_product_partitions_the_product():
+    """C<M> and C<not M> are disjoint and together give A*B exactly; a full
+    mask (or an empty complemented one) leaves A*B unchanged."""
+    rng = np.random.default_rng(5)
+    A = synth.random_sparse(40, 30, 0.1, rng, values="i64")
+    B = synth.random_sparse(30, 25, 0.1, rng, values="i64")
+    M = synth.random_sparse(40, 25, 0.3, rng, values="i64")
+    full = oracle.spgemm(A, B)
+    inside = oracle.spgemm_masked(A, B, M)
+    outside = oracle.spgemm_masked(A, B, M, complement=True)
+    Pi, Po = pattern_dense(inside), pattern_dense(outside)
+    assert not np.any(Pi & Po)
+    assert np.array_equal(Pi | Po, pattern_dense(full))
+    assert np.array_equal(to_dense(inside) + to_dense(outside), to_dense(full))
+    ones = synth.CSC(40, 25, np.arange(26, dtype=np.int64) * 40, np.tile(np.arange(40, dtype=np.int64), 25),
+                     np.ones(1000))
+    empty = synth.CSC(40, 25, np.zeros(26, dtype=np.int64), np.zeros(0, dtype=np.int64), np.zeros(0))
+    for C in (oracle.spgemm_masked(A, B, ones), oracle.spgemm_masked(A, B, empty, complement=True)):
+        assert np.array_equal(C["colptr"], full["colptr"])
+        assert np.array_equal(C["rowidx"], full["rowidx"])
+        assert np.array_equal(C["vals"], full["vals"])
+
+
+def test_masked_product_is_one_bfs_level():
+    """With A a graph and F the current frontier of several sources, A*F
+    under the complement of the visited pattern is the next BFS level: checked
+    against networkx shortest-path lengths."""
+    import networkx as nx
+    A = synth.rmat_symmetric(7, 4, seed=3)
+    G = nx.Graph()
+    G.add_nodes_from(range(A.ncols))
+    for v in range(A.ncols):
+        for u in A.rowidx[A.colptr[v]:A.colptr[v + 1]]:
+            G.add_edge(int(u), v)
+    srcs = [0, 5, 17]
+    dist = [nx.single_source_shortest_path_length(G, s) for s in srcs]
+
+    def level_csc(d):
+        rows = [sorted(v for v, l in dist[c].items() if l == d) for c in range(len(srcs))]
+        cp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+        ri = np.array([v for r in rows for v in r], dtype=np.int64)
+        return synth.CSC(A.nrows, len(srcs), cp, ri, np.ones(ri.shape[0]))
+
+    def visited_csc(d):
+        rows = [sorted(v for v, l in dist[c].items() if l <= d) for c in range(len(srcs))]
+        cp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+        ri = np.array([v for r in rows for v in r], dtype=np.int64)
+        return synth.CSC(A.nrows, len(srcs), cp, ri, np.ones(ri.shape[0]))
+    for d in range(4):
+        nxt = oracle.spgemm_masked(A, level_csc(d), visited_csc(d), complement=True)
+        want = level_csc(d + 1)
+        assert np.array_equal(nxt["colptr"], want.colptr), d
+        assert np.array_equal(nxt["rowidx"], want.rowidx), d
