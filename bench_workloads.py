@@ -484,6 +484,9 @@ def run_bc(args, torch, g, synth):
                 {"sources": 4096, "levels": st["levels"], "frontier_nnz": st["frontier_nnz"],
                  "products_forward": st["products_forward"], "products_backward": st["products_backward"]},
                 level_nnz=levels, ms_forward=st["ms_forward"], ms_backward=st["ms_backward"],
+                spgemm_phase_ms={k: st["ms_" + k] for k in ("plan", "gather", "sym_light", "sym_heavy", "num_light",
+                                                            "num_heavy")},
+                multiplies=st["multiplies"], spgemm_output_nnz=st["nnzC_total"],
                 roofline=roof, cpu_baseline=cpu))
 
 

@@ -412,6 +412,10 @@ typedef struct {
     int64_t products_forward;  /* sparse flops of the forward-search products */
     int64_t products_backward; /* sparse flops of the backward-sweep products */
     double ms_forward, ms_backward;
+    /* sums over all the batch's SpGEMMs of their spg_stats device times */
+    double ms_plan, ms_sym_light, ms_sym_heavy, ms_num_light, ms_num_heavy, ms_gather;
+    int64_t multiplies;        /* SpGEMMs the batch ran */
+    int64_t nnzC_total;        /* sum of their output nonzeros (all inside the masks) */
 } spg_bc_stats;
 
 spg_status spgemm_bc_batch(const spg_csc *A, const int32_t *sources, int32_t s, const spg_options *opt, double *bc,

@@ -399,7 +399,9 @@ def spgemm_outer_multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, 
 class spg_bc_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "levels", "frontier_nnz", "products_forward", "products_backward")] + [
-        (name, ctypes.c_double) for name in ("ms_forward", "ms_backward")]
+        (name, ctypes.c_double) for name in ("ms_forward", "ms_backward", "ms_plan", "ms_sym_light", "ms_sym_heavy",
+                                             "ms_num_light", "ms_num_heavy", "ms_gather")] + [
+        (name, ctypes.c_int64) for name in ("multiplies", "nnzC_total")]
 
 
 def spgemm_bc_batch(A: DeviceCSC, sources: torch.Tensor, P=1, b=1024, bc: torch.Tensor | None = None, stream=None,

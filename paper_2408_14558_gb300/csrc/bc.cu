@@ -126,7 +126,8 @@ struct BcRun {
     }
 };
 
-spg_status multiply_f64(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C, int64_t *products) {
+spg_status multiply_f64(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C, int64_t *products,
+                        spg_bc_stats *S) {
     spg_options o = *opt;
     spg_status s = spgemm_1d_multiply(A, B, &o, C);
     if (s == SPG_OVERFLOW_RECOMPUTED) s = SPG_OK;
@@ -134,6 +135,14 @@ spg_status multiply_f64(const spg_csc *A, const spg_csc *B, const spg_options *o
         spg_stats st{};
         spgemm_last_multiply_stats(&st);
         *products += st.products;
+        S->ms_plan += st.ms_plan;
+        S->ms_sym_light += st.ms_sym_light;
+        S->ms_sym_heavy += st.ms_sym_heavy;
+        S->ms_num_light += st.ms_num_light;
+        S->ms_num_heavy += st.ms_num_heavy;
+        S->ms_gather += st.ms_gather;
+        S->multiplies++;
+        S->nnzC_total += st.nnzC;
     }
     return s;
 }
@@ -228,7 +237,7 @@ extern "C" spg_status spgemm_bc_batch(const spg_csc *A, const int32_t *sources, 
             fo.mask_complement = 1;
             while (true) {
                 spg_csc T{};
-                BC_TRY(multiply_f64(&G, &run.F.back(), &fo, &T, &S.products_forward));
+                BC_TRY(multiply_f64(&G, &run.F.back(), &fo, &T, &S.products_forward, &S));
                 if (T.nnz == 0) {
                     run.free_csc(T);
                     break;
@@ -259,7 +268,7 @@ extern "C" spg_status spgemm_bc_batch(const spg_csc *A, const int32_t *sources, 
             bo.mask_words = W;
             bo.mask_complement = 0;
             spg_csc T{};
-            BC_TRY(multiply_f64(&G, &Wd, &bo, &T, &S.products_backward));
+            BC_TRY(multiply_f64(&G, &Wd, &bo, &T, &S.products_backward, &S));
             run.delta[d - 1] = (double *)alloc_user(opt, 8 * (size_t)std::max<int64_t>(Fp.nnz, 1));
             if (!run.delta[d - 1]) {
                 run.free_csc(T);

@@ -51,6 +51,7 @@ int main(void) {
          offsetof(spg_options, learned_slack), offsetof(spg_stats, ms_plan));
   printf("%zu %zu\\n", sizeof(spg_outer_stats), offsetof(spg_outer_stats, ms_split));
   printf("%zu %zu\\n", offsetof(spg_options, mask), offsetof(spg_options, mask_complement));
+  printf("%zu %zu\\n", sizeof(spg_bc_stats), offsetof(spg_bc_stats, nnzC_total));
   return 0;
 }
 """)
@@ -69,6 +70,8 @@ int main(void) {
     assert sizes[8] == g.spg_outer_stats.ms_split.offset
     assert sizes[9] == g.spg_options.mask.offset
     assert sizes[10] == g.spg_options.mask_complement.offset
+    assert sizes[11] == ctypes.sizeof(g.spg_bc_stats)
+    assert sizes[12] == g.spg_bc_stats.nnzC_total.offset
 
 
 def test_default_options(lib):
