@@ -63,6 +63,21 @@ def test_heavy_slabs(light_max, slab, vals):
     assert_full_parity(C, ref, f"heavy {light_max} {slab} {vals}")
 
 
+@pytest.mark.parametrize("vals", ["f64", "i64"])
+def test_heavy_slabs_int64_indices(vals):
+    """The dense-slab kernels with int64 row ids and column pointers (their
+    64-bit output-index instances), several items per column."""
+    rng = np.random.default_rng(21)
+    m = 9000
+    A = synth.random_sparse(m, 500, 0.012, rng, values="f64" if vals == "f64" else "i64big")
+    B = synth.random_sparse(500, 300, 0.12, rng, values="f64" if vals == "f64" else "i64big")
+    ref = oracle.spgemm(A, B)
+    assert ref["nnz"].max() > 4096          # some columns span two numeric items
+    C = run_gpu(A, B, 3, 64, ptr=torch.int64, idx=torch.int64, light_max=32, slab_rows=1024)
+    assert C.rowidx.dtype == torch.int64
+    assert_full_parity(C, ref, f"heavy int64 indices {vals}")
+
+
 def test_banded_windows():
     """Clustered rows (a banded A) give narrow row windows: light bins hold
     columns with many products but few distinct rows."""
