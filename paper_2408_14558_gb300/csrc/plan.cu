@@ -152,33 +152,36 @@ enum {
     kCntSlots = 24
 };
 
-__global__ void k_validate(const void *colptr, int p64, const void *rowidx, int i64, int64_t nrows,
-                           int64_t ncols, int64_t nnz, int *err) {
-    int lane = threadIdx.x & 31;
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    if (warp == 0 && lane == 0) {
-        if (ld_ptr(colptr, p64, 0) != 0 || ld_ptr(colptr, p64, ncols) != nnz) atomicOr(err, kDevErrInput);
+// Input checks, in two passes that read the matrix once, coalesced.
+// Per column: 0 <= colptr[j] <= colptr[j+1] <= nnz, colptr[0] = 0 and
+// colptr[ncols] = nnz; the first entry of every non-empty column is marked in
+// `starts` (one bit per entry, zeroed by the caller).
+__global__ void k_validate_cols(const void *colptr, int p64, int64_t ncols, int64_t nnz, uint32_t *starts,
+                                int *err) {
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0 && (ld_ptr(colptr, p64, 0) != 0 || ld_ptr(colptr, p64, ncols) != nnz)) atomicOr(err, kDevErrInput);
+    for (int64_t j = t0; j < ncols; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
+        if (s > e || s < 0 || e > nnz)
+            atomicOr(err, kDevErrInput);
+        else if (s < e)
+            atomicOr(starts + (s >> 5), 1u << (s & 31));
     }
-    for (int64_t j = warp; j < ncols; j += nwarps) {
-        int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
-        bool bad = (s > e) || (s < 0) || (e > nnz);
-        if (!bad) {
-            for (int64_t q0 = s + lane; q0 < e; q0 += 32 * 4) {
-                int64_t r[4], pr[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int64_t q = q0 + 32 * u;
-                    r[u] = q < e ? ld_ptr(rowidx, i64, q) : 0;
-                    pr[u] = (q < e && q > s) ? ld_ptr(rowidx, i64, q - 1) : -1;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (r[u] < 0 || r[u] >= nrows || pr[u] >= r[u]) bad = true;
-            }
-        }
-        if (__any_sync(kFull, bad) && lane == 0) atomicOr(err, kDevErrInput);
+}
+
+// Per entry: 0 <= row < nrows, and rows strictly increase inside a column: a
+// row not above its predecessor is allowed only where a column starts.
+__global__ void k_validate_rows(const void *rowidx, int i64, int64_t nnz, int64_t nrows,
+                                const uint32_t *__restrict__ starts, int *err) {
+    bool bad = false;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = ld_ptr(rowidx, i64, q);
+        if (r < 0 || r >= nrows)
+            bad = true;
+        else if (q > 0 && ld_ptr(rowidx, i64, q - 1) >= r && !((starts[q >> 5] >> (q & 31)) & 1u))
+            bad = true;
     }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kDevErrInput);
 }
 
 __global__ void k_nonempty_bits(const void *colptr, int p64, int64_t k, int64_t W, uint32_t *D) {
@@ -825,10 +828,19 @@ static spg_status plan_build(spg_plan *p) {
     cudaEventRecord(p->ev[0], st);
 
     if (p->opt.validate) {
-        launch(p, k_validate, grid_for(A.ncols * 32, 256, sm * 16), 256, 0, A.colptr, p64A, A.rowidx, i64A, A.nrows,
-                                                                          A.ncols, A.nnz, p->d_err);
-        launch(p, k_validate, grid_for(B.ncols * 32, 256, sm * 16), 256, 0, B.colptr, p64B, B.rowidx, i64B, B.nrows,
-                                                                          B.ncols, B.nnz, p->d_err);
+        const int64_t sw = (std::max<int64_t>(A.nnz, B.nnz) + 31) / 32 + 1;
+        uint32_t *starts = (uint32_t *)ws_alloc(p, sizeof(uint32_t) * (size_t)sw);
+        if (!starts) return SPG_OUT_OF_MEMORY;
+        const spg_csc *M[2] = {&A, &B};
+        for (int i = 0; i < 2; i++) {
+            const int pp = M[i]->ptr_type == SPG_IDX_I64, ii = M[i]->idx_type == SPG_IDX_I64;
+            TRY(cuda_check(cudaMemsetAsync(starts, 0, sizeof(uint32_t) * (size_t)sw, st), "memset"));
+            launch(p, k_validate_cols, grid_for(M[i]->ncols + 1, 256, sm * 8), 256, 0, M[i]->colptr, pp,
+                   M[i]->ncols, M[i]->nnz, starts, p->d_err);
+            if (M[i]->nnz > 0)
+                launch(p, k_validate_rows, grid_for(M[i]->nnz, 256, sm * 16), 256, 0, M[i]->rowidx, ii, M[i]->nnz,
+                       M[i]->nrows, (const uint32_t *)starts, p->d_err);
+        }
         LAUNCH_OK("validate");
         TRY(read_dev_err(p, "input validation"));
     }

@@ -176,6 +176,28 @@ def test_invalid_input_is_rejected():
     with pytest.raises(g.SpgError) as e:
         run_gpu(A, oob, 2, 4)
     assert e.value.status == g.SPG_INVALID_INPUT
+    dup = synth.CSC(B.nrows, B.ncols, B.colptr, B.rowidx.copy(), B.vals)
+    dup.rowidx[s + 1] = dup.rowidx[s]                                     # repeated row in a column
+    with pytest.raises(g.SpgError) as e:
+        run_gpu(A, dup, 2, 4)
+    assert e.value.status == g.SPG_INVALID_INPUT
+    cp = B.colptr.copy()
+    j2 = int(np.flatnonzero(np.diff(cp) >= 1)[-1])                        # the last non-empty column
+    cp[j2], cp[j2 + 1] = cp[j2 + 1], cp[j2]                               # column pointers out of order
+    with pytest.raises(g.SpgError) as e:
+        run_gpu(A, synth.CSC(B.nrows, B.ncols, cp, B.rowidx, B.vals), 2, 4)
+    assert e.value.status == g.SPG_INVALID_INPUT
+
+
+def test_rows_may_fall_between_columns():
+    """Canonical input whose row ids drop from one column to the next, also
+    across empty columns and at a column holding the same first row: accepted."""
+    cols = [[5, 9], [], [], [0, 9], [9], [], [1], [0, 1, 2]]
+    cp = np.cumsum([0] + [len(c) for c in cols]).astype(np.int64)
+    ri = np.array([r for c in cols for r in c], dtype=np.int32)
+    B = synth.CSC(10, len(cols), cp, ri, np.arange(1, ri.size + 1, dtype=np.float64))
+    A = synth.random_sparse(12, 10, 0.4, np.random.default_rng(2), values="small")
+    assert_full_parity(run_gpu(A, B, 3, 4), oracle.spgemm(A, B), "row drops at column starts")
 
 
 def test_one_call_multiply_and_stats():
