@@ -2,7 +2,9 @@
 // for all P column blocks at once, on one GPU.
 //   k_nonempty_bits  D, the nonempty columns of A (Algorithm 1, allgather of
 //                    nonzero column ids: here A.colptr is local)
-//   k_mark_H         H_i, nonzero rows of B_i (Table 1, Algorithm 1)
+//   k_block_eoff     the first entry of B of every column block
+//   k_mark_H         H_i, nonzero rows of B_i (Table 1, Algorithm 1), one
+//                    thread per entry of B
 //   k_popc_HD        popc(H_i & D) per word, then a scan gives each required
 //                    column its place in D~ (Algorithm 1, D~ = H_i AND D)
 //   k_dtilde         the ascending list D~_i
@@ -258,23 +260,33 @@ __global__ void k_block_flops(const int64_t *flops, int64_t n, int P, const int6
 }
 
 // Warp per column j of B: set bit r of H_{block(j)} for every stored row r.
-__global__ void k_mark_H(const void *colptr, int p64, const void *rowidx, int i64, int64_t n, int P,
-                         int64_t W, uint32_t *H, const int64_t *bounds) {
-    int lane = threadIdx.x & 31;
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = warp; j < n; j += nwarps) {
-        int i = block_of_b(j, n, P, bounds);
-        uint32_t *Hi = H + (int64_t)i * W;
-        int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
-        for (int64_t q0 = s + lane; q0 < e; q0 += 32 * 8) {
-            int64_t r[8];
-#pragma unroll
-            for (int u = 0; u < 8; u++) r[u] = q0 + 32 * u < e ? ld_ptr(rowidx, i64, q0 + 32 * u) : -1;
-#pragma unroll
-            for (int u = 0; u < 8; u++)
-                if (r[u] >= 0) atomicOr(Hi + (r[u] >> 5), 1u << (r[u] & 31));
-        }
+// First entry of every column block of B: eoff[i] = colptr[bound_i], i <= P.
+__global__ void k_block_eoff(const void *colptr, int p64, int64_t n, int P, const int64_t *bounds, int64_t *eoff) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= P; i += gridDim.x * blockDim.x)
+        eoff[i] = ld_ptr(colptr, p64, bounds ? bounds[i] : (int64_t)i * n / P);
+}
+
+// The column block of B's entry q: the largest i < P with eoff[i] <= q
+// (empty blocks share their offset with the next one).
+__device__ __forceinline__ int block_of_entry(int64_t q, const int64_t *__restrict__ eoff, int P) {
+    int lo = 0, hi = P;  // eoff[lo] <= q < eoff[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(eoff + mid) <= q)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// H_i: one atomicOr per entry of B into its block's bitmap (entry-parallel).
+__global__ void k_mark_H(const void *rowidx, int i64, int64_t nnz, int P, int64_t W, uint32_t *H,
+                         const int64_t *__restrict__ eoff) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = ld_ptr(rowidx, i64, q);
+        const int i = block_of_entry(q, eoff, P);
+        atomicOr(H + (int64_t)i * W + (r >> 5), 1u << (r & 31));
     }
 }
 
@@ -469,40 +481,23 @@ __global__ void k_gather_copy(const int64_t *__restrict__ At_colptr, const int64
     }
 }
 
-// Warp per column j: each row k of B_i becomes its column index in A~ (or -1).
+// Every entry of B_i (entry-parallel): its row k becomes its column index in
+// A~ (or -1 when A(:, k) is empty), its value the accumulation type.
 template <typename Acc>
-__global__ void k_remap_B(const void *colptr, int p64, const void *rowidx, int i64, const void *vals,
-                          int vt, int64_t n, int P, const uint32_t *H, const uint32_t *D,
-                          const int64_t *rankpre, int64_t W, int32_t *Bq, Acc *Bv, const int64_t *bounds) {
-    int lane = threadIdx.x & 31;
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = warp; j < n; j += nwarps) {
-        int i = block_of_b(j, n, P, bounds);
-        int64_t s = ld_ptr(colptr, p64, j), e = ld_ptr(colptr, p64, j + 1);
-        for (int64_t q0 = s + lane; q0 < e; q0 += 32 * 4) {
-            int64_t r[4];
-            uint32_t word[4];
-            int64_t pre[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) r[u] = q0 + 32 * u < e ? ld_ptr(rowidx, i64, q0 + 32 * u) : -1;
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int64_t w = r[u] >= 0 ? r[u] >> 5 : 0;
-                word[u] = r[u] >= 0 ? H[(int64_t)i * W + w] & D[w] : 0;
-                pre[u] = r[u] >= 0 ? rankpre[(int64_t)i * W + w] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int64_t q = q0 + 32 * u;
-                if (q >= e) continue;
-                const uint32_t sh = (uint32_t)(r[u] & 31);
-                int32_t loc = -1;
-                if ((word[u] >> sh) & 1u) loc = (int32_t)(pre[u] + __popc(word[u] & ((1u << sh) - 1u)));
-                Bq[q] = loc;
-                Bv[q] = load_val<Acc>(vals, vt, q);
-            }
-        }
+__global__ void k_remap_B(const void *rowidx, int i64, const void *vals, int vt, int64_t nnz, int P,
+                          const uint32_t *__restrict__ H, const uint32_t *__restrict__ D,
+                          const int64_t *__restrict__ rankpre, int64_t W, int32_t *Bq, Acc *Bv,
+                          const int64_t *__restrict__ eoff) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = ld_ptr(rowidx, i64, q);
+        const int i = block_of_entry(q, eoff, P);
+        const int64_t w = r >> 5;
+        const uint32_t word = H[(int64_t)i * W + w] & D[w];
+        const uint32_t sh = (uint32_t)(r & 31);
+        int32_t loc = -1;
+        if ((word >> sh) & 1u) loc = (int32_t)(rankpre[(int64_t)i * W + w] + __popc(word & ((1u << sh) - 1u)));
+        Bq[q] = loc;
+        Bv[q] = load_val<Acc>(vals, vt, q);
     }
 }
 
@@ -743,9 +738,9 @@ __global__ void k_split(const int64_t *At_colptr, const int32_t *At_row, int64_t
 spg_status copy_operands(spg_plan *p) {
     const spg_csc &A = p->A, &B = p->B;
     const int sm = p->sm_count, P = p->P;
-    const int64_t n = p->n, W = p->W;
+    const int64_t W = p->W;
     const int p64A = A.ptr_type == SPG_IDX_I64, i64A = A.idx_type == SPG_IDX_I64;
-    const int p64B = B.ptr_type == SPG_IDX_I64, i64B = B.idx_type == SPG_IDX_I64;
+    const int i64B = B.idx_type == SPG_IDX_I64;
     if (p->ndt > 0 && p->nAt > 0) {
         if (!p->gshift) p->gshift = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)p->ndt);
         if (!p->gshift) return SPG_OUT_OF_MEMORY;
@@ -766,14 +761,14 @@ spg_status copy_operands(spg_plan *p) {
         spg_status s = cuda_check(cudaGetLastError(), "gather");
         if (s) return s;
     }
-    if (n > 0) {
-        int g = grid_for(n * 32, 256, sm * 16);
+    if (B.nnz > 0) {
+        int g = grid_for(B.nnz, 256, sm * 16);
         if (p->acc_f64)
-            launch(p, k_remap_B<double>, g, 256, 0, B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P, p->Hbits,
-                   p->Dbits, p->rankpre, W, p->Bq, (double *)p->Bv, p->bounds_d);
+            launch(p, k_remap_B<double>, g, 256, 0, B.rowidx, i64B, B.vals, B.val_type, B.nnz, P, p->Hbits, p->Dbits,
+                   p->rankpre, W, p->Bq, (double *)p->Bv, (const int64_t *)p->eoff);
         else
-            launch(p, k_remap_B<long long>, g, 256, 0, B.colptr, p64B, B.rowidx, i64B, B.vals, B.val_type, n, P,
-                   p->Hbits, p->Dbits, p->rankpre, W, p->Bq, (long long *)p->Bv, p->bounds_d);
+            launch(p, k_remap_B<long long>, g, 256, 0, B.rowidx, i64B, B.vals, B.val_type, B.nnz, P, p->Hbits,
+                   p->Dbits, p->rankpre, W, p->Bq, (long long *)p->Bv, (const int64_t *)p->eoff);
         return cuda_check(cudaGetLastError(), "remap B");
     }
     return SPG_OK;
@@ -815,7 +810,7 @@ static spg_status plan_build(spg_plan *p) {
     const int64_t m = p->m, k = p->k, n = p->n;
     const int P = p->P;
     const int sm = p->sm_count;
-    const int p64A = A.ptr_type == SPG_IDX_I64, i64A = A.idx_type == SPG_IDX_I64;
+    const int p64A = A.ptr_type == SPG_IDX_I64;
     const int p64B = B.ptr_type == SPG_IDX_I64, i64B = B.idx_type == SPG_IDX_I64;
     const size_t accsz = 8;
 
@@ -878,11 +873,15 @@ static spg_status plan_build(spg_plan *p) {
     p->nfb = (k + p->b - 1) / p->b;
     p->fetch = (uint8_t *)ws_alloc(p, (size_t)(P * p->nfb + 1));
     if (!p->Dbits || !p->Hbits || !p->rankpre || !popc || !p->fetch) return SPG_OUT_OF_MEMORY;
+    p->eoff = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(P + 1));
+    if (!p->eoff) return SPG_OUT_OF_MEMORY;
     TRY(cuda_check(cudaMemsetAsync(p->Hbits, 0, sizeof(uint32_t) * (size_t)(P * W + 1), st), "memset H"));
     if (W > 0) launch(p, k_nonempty_bits, grid_for(W, 256, sm * 8), 256, 0, A.colptr, p64A, k, W, p->Dbits);
-    if (n > 0)
-        launch(p, k_mark_H, grid_for(n * 32, 256, sm * 16), 256, 0, B.colptr, p64B, B.rowidx, i64B, n, P, W, p->Hbits,
-               p->bounds_d);
+    launch(p, k_block_eoff, grid_for(P + 1, 256, sm), 256, 0, B.colptr, p64B, n, P, (const int64_t *)p->bounds_d,
+           p->eoff);
+    if (B.nnz > 0)
+        launch(p, k_mark_H, grid_for(B.nnz, 256, sm * 16), 256, 0, B.rowidx, i64B, B.nnz, P, W, p->Hbits,
+               (const int64_t *)p->eoff);
     LAUNCH_OK("mark H");
 
     // --- step 2: D~_i = H_i & D, its ranks and Algorithm 2

@@ -133,6 +133,7 @@ struct spg_plan {
     int32_t *nbinlist = nullptr;
     void *num_items = nullptr;  // one header per numeric item (k_num_heavy)
     int64_t *bounds_d = nullptr;     // column block bounds (P + 1) of a non-uniform split, else null
+    int64_t *eoff = nullptr;         // first entry of B of every column block (P + 1)
     std::vector<int64_t> bounds_h;   // the bounds in effect (P + 1), host
     int64_t *blk = nullptr;          // per block: flops, gathered A~ nonzeros, of them fetched (3 x P)
     int64_t *gshift = nullptr;       // per A~ column: its entries' offset into A (gather)
