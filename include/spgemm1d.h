@@ -434,6 +434,36 @@ typedef struct {
 spg_status spgemm_outer_multiply(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C,
                                  spg_outer_stats *stats);
 
+/*
+ * C = A * B (Algorithm 1, exact sizing) for matrices in HOST memory, the
+ * host-device copies inside the call.  A and B are spg_csc with host pointers
+ * (pinned memory for full copy speed; any types spgemm_plan accepts); when B
+ * names the same host arrays as A they are copied once.  B's columns are cut
+ * into min(chunks, P, n) groups of consecutive column blocks (group g holds
+ * blocks [g*P/G, (g+1)*P/G) of the uniform split and multiplies them as a
+ * plan of its own); all groups are planned and counted, C's three host
+ * arrays are requested from host_alloc (column pointers int64 n + 1, rows of
+ * A's idx_type, values double or int64; NULL from it gives SPG_OUT_OF_MEMORY),
+ * then each group's numeric pass runs on opt->stream while the previous
+ * group's part of C is copied to the host on a stream of the call's own.
+ * Device workspace and device copies come from opt->alloc / opt->free (or
+ * cudaMallocAsync) and are released before returning; opt->mask, if set,
+ * applies as in spgemm_plan (its columns are C's columns).  Blocks until C is
+ * on the host; on success C describes the host arrays, which belong to the
+ * caller; on failure any array host_alloc returned is handed to host_free
+ * (which may be NULL) and C is untouched.  spgemm_last_multiply_stats then
+ * holds the counters and device times summed over the groups.  Errors:
+ * SPG_INVALID_ARGUMENT for NULL options / C / host_alloc, chunks < 1, learned
+ * sizing, a dimension mismatch or a host colptr whose first entry is not 0 or
+ * whose last is not nnz; otherwise as spgemm_plan, spgemm_symbolic and
+ * spgemm_numeric.
+ */
+typedef void *(*spg_host_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*spg_host_free_fn)(void *ptr, size_t bytes, void *ctx);
+spg_status spgemm_1d_multiply_host(const spg_csc *A, const spg_csc *B, const spg_options *opt, int32_t chunks,
+                                   spg_host_alloc_fn host_alloc, spg_host_free_fn host_free, void *host_ctx,
+                                   spg_csc *C);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@ import os
 import threading
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -371,6 +372,114 @@ class spg_outer_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "P", "products", "nnzB_moved", "partial_nnz", "partial_moved", "nnzC")] + [
         (name, ctypes.c_double) for name in ("ms_split", "ms_local", "ms_merge")]
+
+
+# ----------------------------------------------------- host-buffer multiply
+
+HOST_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+HOST_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+_HOST_IDX = {np.dtype(np.int32): SPG_IDX_I32, np.dtype(np.int64): SPG_IDX_I64}
+_HOST_VAL = {np.dtype(np.float64): SPG_VAL_F64, np.dtype(np.int32): SPG_VAL_I32, np.dtype(np.int64): SPG_VAL_I64}
+
+
+def _host_array(a):
+    """(address, numpy dtype, length) of a contiguous CPU torch tensor or numpy array."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("host arrays must be contiguous CPU tensors")
+        return a.data_ptr(), np.dtype(str(a.dtype).replace("torch.", "")), a.numel()
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data, a.dtype, a.size
+
+
+def _host_csc(M) -> spg_csc:
+    cp, cpt, _ = _host_array(M.colptr)
+    ri, rit, nnz = _host_array(M.rowidx)
+    va, vat, _ = _host_array(M.vals)
+    return spg_csc(int(M.nrows), int(M.ncols), int(nnz), _HOST_IDX[cpt], _HOST_IDX[rit], _HOST_VAL[vat], 0, cp,
+                   ri if nnz else None, va if nnz else None)
+
+
+class HostPool:
+    """Pinned host memory carved into the arrays of a host-buffer product:
+    reused from call to call (the previous result's arrays are overwritten)."""
+
+    def __init__(self, nbytes: int):
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, pin_memory=True)
+        self.used = 0
+
+    def take(self, nbytes: int):
+        start = (self.used + 255) & ~255
+        if start + nbytes > self.buf.numel():
+            return None
+        self.used = start + nbytes
+        return self.buf[start:start + nbytes]
+
+
+class HostCSC:
+    """A product in host memory: colptr (int64), rowidx (the inputs' index
+    type) and vals (double or int64) as CPU tensors over pinned buffers."""
+
+    def __init__(self, nrows, ncols, colptr, rowidx, vals, keep):
+        self.nrows, self.ncols = nrows, ncols
+        self.colptr, self.rowidx, self.vals = colptr, rowidx, vals
+        self._keep = keep
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowidx.numel())
+
+    @property
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in (self.colptr, self.rowidx, self.vals))
+
+
+def spgemm_1d_multiply_host(A, B, P=1, b=1024, chunks=4, stream=None, validate=True, light_max=0, slab_rows=0,
+                            split=0, pool: HostPool | None = None, mask=None, mask_complement=False) -> HostCSC:
+    """C = A * B for host matrices (objects with nrows, ncols and colptr /
+    rowidx / vals as CPU tensors or numpy arrays; pinned memory for full copy
+    speed) through spgemm_1d_multiply_host: the copies to and from the GPU
+    happen inside the call, C's part of one group of column blocks streaming
+    back while the next group computes.  C's arrays come from `pool` when
+    given (its earlier contents are overwritten), else from fresh pinned
+    tensors.  mask: an optional output mask on the GPU (as for spgemm_plan)."""
+    lib = load_library()
+    lib.spgemm_1d_multiply_host.argtypes = [ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc),
+                                            ctypes.POINTER(spg_options), ctypes.c_int32, HOST_ALLOC_FN,
+                                            HOST_FREE_FN, ctypes.c_void_p, ctypes.POINTER(spg_csc)]
+    lib.spgemm_1d_multiply_host.restype = ctypes.c_int
+    alloc = _TorchAllocator(torch.device("cuda", torch.cuda.current_device()))
+    mp, mw = _mask_fields(mask, int(A.nrows), int(B.ncols))
+    opts = make_options(P, b, stream, validate, light_max, slab_rows, allocator=alloc, split=split, mask=mp,
+                        mask_words=mw, mask_complement=mask_complement)
+    if pool is not None:
+        pool.used = 0
+    held = {}
+
+    def host_alloc(nbytes, ctx):
+        t = pool.take(nbytes) if pool is not None else torch.empty(int(nbytes), dtype=torch.uint8, pin_memory=True)
+        if t is None:
+            return None
+        held[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def host_free(ptr, nbytes, ctx):
+        held.pop(ptr, None)
+
+    ha, hb = _host_csc(A), _host_csc(B)
+    c = spg_csc()
+    fa, ff = HOST_ALLOC_FN(host_alloc), HOST_FREE_FN(host_free)
+    _check(lib.spgemm_1d_multiply_host(ctypes.byref(ha), ctypes.byref(hb), ctypes.byref(opts), int(chunks), fa, ff,
+                                       None, ctypes.byref(c)))
+    idx_dt = torch.int64 if c.idx_type == SPG_IDX_I64 else torch.int32
+    val_dt = torch.float64 if c.val_type == SPG_VAL_F64 else torch.int64
+
+    def view(addr, dt, count):
+        base = held[addr]
+        return base[: count * torch.tensor([], dtype=dt).element_size()].view(dt)
+    return HostCSC(c.nrows, c.ncols, view(c.colptr, torch.int64, c.ncols + 1), view(c.rowidx, idx_dt, c.nnz),
+                   view(c.vals, val_dt, c.nnz), (held, pool))
 
 
 def spgemm_outer_multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, stream=None, validate=True, light_max=0,

@@ -324,21 +324,29 @@ static spg_status numeric_typed(spg_plan *p, spg_csc *C) {
     return s;
 }
 
+// The light columns' numeric bins (by their exact counts), once per plan: the
+// only step of the numeric pass that reads back to the host (the bin sizes).
+spg_status prepare_numeric(spg_plan *p) {
+    const int64_t n = p->n;
+    if (p->nbinlist) return SPG_OK;
+    int8_t *bn = (int8_t *)ws_alloc(p, (size_t)(n + 1));
+    p->nbinlist = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(n + 1));
+    if (!bn || !p->nbinlist) return SPG_OUT_OF_MEMORY;
+    if (n > 0) {
+        launch(p, k_rebin_numeric, grid_for(n, 256, p->sm_count * 8), 256, 0, p->bin_of, p->nnzcol, n, bn);
+        spg_status s = cuda_check(cudaGetLastError(), "rebin");
+        if (s) return s;
+        s = bin_columns(p, bn, p->nbinlist, p->nbin_off);
+        if (s) return s;
+    }
+    return SPG_OK;
+}
+
 spg_status run_numeric(spg_plan *p, spg_csc *C) {
     cudaStream_t st = p->st;
     const int64_t n = p->n;
-    if (!p->nbinlist) {
-        int8_t *bn = (int8_t *)ws_alloc(p, (size_t)(n + 1));
-        p->nbinlist = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)(n + 1));
-        if (!bn || !p->nbinlist) return SPG_OUT_OF_MEMORY;
-        if (n > 0) {
-            launch(p, k_rebin_numeric, grid_for(n, 256, p->sm_count * 8), 256, 0, p->bin_of, p->nnzcol, n, bn);
-            spg_status s = cuda_check(cudaGetLastError(), "rebin");
-            if (s) return s;
-            s = bin_columns(p, bn, p->nbinlist, p->nbin_off);
-            if (s) return s;
-        }
-    }
+    spg_status s0 = prepare_numeric(p);
+    if (s0) return s0;
     if (C->colptr && C->colptr != (void *)p->Ccolptr) {
         spg_status s = cuda_check(cudaMemcpyAsync(C->colptr, p->Ccolptr, sizeof(int64_t) * (size_t)(n + 1),
                                                   cudaMemcpyDeviceToDevice, st),

@@ -192,6 +192,7 @@ spg_status cuda_check(cudaError_t e, const char *what);
 void *ws_alloc(spg_plan *p, size_t bytes);
 void ws_free_all(spg_plan *p);
 spg_status copy_operands(spg_plan *p);
+spg_status prepare_numeric(spg_plan *p);
 // Memory handed to the caller (C's arrays): through opt->alloc, else cudaMallocAsync.
 void *alloc_user(const spg_options *opt, size_t bytes);
 spg_status read_dev_err(spg_plan *p, const char *phase);

@@ -188,3 +188,40 @@ def test_mask_argument_errors_need_no_gpu(lib):
     fake = ctypes.c_double(0.0)
     assert fb(ctypes.byref(G), None, 0, ctypes.byref(o), ctypes.addressof(fake), None, 0, None) == g.SPG_INVALID_ARGUMENT
     assert "mask" in g.spgemm_last_error()
+
+
+def test_host_multiply_argument_errors_need_no_gpu(lib):
+    """spgemm_1d_multiply_host checks its arguments (and the host column
+    pointers' first and last entries) before any CUDA call."""
+    import numpy as np
+    import paper_2408_14558_gb300 as g
+    f = lib.spgemm_1d_multiply_host
+    f.argtypes = [ctypes.POINTER(g.spg_csc), ctypes.POINTER(g.spg_csc), ctypes.POINTER(g.spg_options), ctypes.c_int32,
+                  g.HOST_ALLOC_FN, g.HOST_FREE_FN, ctypes.c_void_p, ctypes.POINTER(g.spg_csc)]
+    f.restype = ctypes.c_int
+    cp = np.array([0, 2, 3], dtype=np.int64)
+    ri = np.array([0, 1, 1], dtype=np.int32)
+    va = np.ones(3)
+    A = g.spg_csc(2, 2, 3, 1, 0, 0, 0, cp.ctypes.data, ri.ctypes.data, va.ctypes.data)
+    o = g.spg_options()
+    lib.spgemm_default_options(ctypes.byref(o))
+    C = g.spg_csc()
+    never = g.HOST_ALLOC_FN(lambda n, ctx: None)
+    nofree = g.HOST_FREE_FN(lambda p, n, ctx: None)
+    null_alloc = ctypes.cast(None, g.HOST_ALLOC_FN)
+    assert f(ctypes.byref(A), ctypes.byref(A), ctypes.byref(o), 1, null_alloc, nofree, None, ctypes.byref(C)) \
+        == g.SPG_INVALID_ARGUMENT
+    assert f(ctypes.byref(A), ctypes.byref(A), ctypes.byref(o), 0, never, nofree, None, ctypes.byref(C)) \
+        == g.SPG_INVALID_ARGUMENT
+    bad = np.array([0, 2, 2], dtype=np.int64)                   # last pointer != nnz
+    Ab = g.spg_csc(2, 2, 3, 1, 0, 0, 0, bad.ctypes.data, ri.ctypes.data, va.ctypes.data)
+    assert f(ctypes.byref(Ab), ctypes.byref(A), ctypes.byref(o), 1, never, nofree, None, ctypes.byref(C)) \
+        == g.SPG_INVALID_ARGUMENT
+    B3 = g.spg_csc(3, 2, 3, 1, 0, 0, 0, cp.ctypes.data, ri.ctypes.data, va.ctypes.data)   # 2 != 3
+    assert f(ctypes.byref(A), ctypes.byref(B3), ctypes.byref(o), 1, never, nofree, None, ctypes.byref(C)) \
+        == g.SPG_INVALID_ARGUMENT
+    assert "dimension mismatch" in g.spgemm_last_error()
+    o.sizing = g.SPG_SIZING_LEARNED
+    assert f(ctypes.byref(A), ctypes.byref(A), ctypes.byref(o), 1, never, nofree, None, ctypes.byref(C)) \
+        == g.SPG_INVALID_ARGUMENT
+    assert C.colptr is None
