@@ -368,8 +368,12 @@ def main(argv=None):
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     if not args.no_e2e:
-        line["e2e"] = run_e2e(g, torch, A, Ai, max(1, min(args.steps, 3)), world, products_step,
-                              max(st["nnzC"] for sts in stats for st in sts))
+        try:
+            line["e2e"] = run_e2e(g, torch, A, Ai, max(1, min(args.steps, 3)), world, products_step,
+                                  max(st["nnzC"] for sts in stats for st in sts))
+        except RuntimeError as ex:   # e.g. no room for C's pinned host pool on this machine (SpgError too)
+            line["e2e"] = {"value": None, "unit": "GFLOP/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                           "error": str(ex).splitlines()[0][:300]}
 
     if rank == 0:
         print(json.dumps(line), flush=True)
