@@ -225,3 +225,25 @@ def test_host_multiply_argument_errors_need_no_gpu(lib):
     assert f(ctypes.byref(A), ctypes.byref(A), ctypes.byref(o), 1, never, nofree, None, ctypes.byref(C)) \
         == g.SPG_INVALID_ARGUMENT
     assert C.colptr is None
+
+
+def test_host_csc_marshalling():
+    """The host-buffer call's descriptors: addresses, sizes and type codes of
+    numpy arrays and CPU tensors."""
+    import numpy as np
+    import torch
+    import paper_2408_14558_gb300 as g
+    import synth
+    M = synth.random_sparse(7, 5, 0.4, np.random.default_rng(0), values="i64")
+    d = g._host_csc(M)
+    assert (d.nrows, d.ncols, d.nnz) == (7, 5, M.nnz)
+    assert (d.ptr_type, d.idx_type, d.val_type) == (g.SPG_IDX_I64, g.SPG_IDX_I32, g.SPG_VAL_I64)
+    assert d.colptr == M.colptr.ctypes.data and d.rowidx == M.rowidx.ctypes.data
+    T = synth.CSC(7, 5, torch.from_numpy(M.colptr.astype(np.int32)), torch.from_numpy(M.rowidx.astype(np.int64)),
+                  torch.from_numpy(M.vals.astype(np.float64)))
+    d = g._host_csc(T)
+    assert (d.ptr_type, d.idx_type, d.val_type) == (g.SPG_IDX_I32, g.SPG_IDX_I64, g.SPG_VAL_F64)
+    assert d.vals == T.vals.data_ptr()
+    E = synth.CSC(3, 2, np.zeros(3, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    d = g._host_csc(E)
+    assert d.nnz == 0 and d.rowidx is None and d.vals is None
