@@ -280,6 +280,9 @@ extern "C" spg_status spgemm_1d_multiply_host(const spg_csc *A, const spg_csc *B
     }
     if (s) {
         std::string keep = last_error_str();
+        // copies already queued may still be writing into C's host arrays
+        cudaStreamSynchronize(run.copy);
+        cudaStreamSynchronize(st);
         give_back();
         set_error("%s", keep.c_str());
         return s;
