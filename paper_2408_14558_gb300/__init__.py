@@ -403,11 +403,30 @@ def _host_csc(M) -> spg_csc:
 
 class HostPool:
     """Pinned host memory carved into the arrays of a host-buffer product:
-    reused from call to call (the previous result's arrays are overwritten)."""
+    reused from call to call (the previous result's arrays are overwritten).
+    Exactly `nbytes` are page-locked (a host buffer registered with CUDA);
+    torch's pinned allocator, which rounds sizes up to a power of two, is the
+    fallback when registration fails."""
 
     def __init__(self, nbytes: int):
-        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, pin_memory=True)
+        nbytes = int(nbytes)
+        self._host = None
         self.used = 0
+        host = np.empty(nbytes, dtype=np.uint8)
+        rt = torch.cuda.cudart()
+        if nbytes > 0 and int(rt.cudaHostRegister(host.ctypes.data, nbytes, 0)) == 0:
+            self._host, self._rt = host, rt
+            self.buf = torch.from_numpy(host)
+        else:
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+
+    def __del__(self):
+        if getattr(self, "_host", None) is not None:
+            try:
+                self._rt.cudaHostUnregister(self._host.ctypes.data)
+            except Exception:
+                pass
+            self._host = None
 
     def take(self, nbytes: int):
         start = (self.used + 255) & ~255
