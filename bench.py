@@ -160,15 +160,18 @@ class ClockSampler:
 
 # ------------------------------------------------------------ CPU baseline
 
-def time_oracle(A, ncols_sample: int, seed: int):
+def time_oracle(A, ncols_sample: int, seed: int, nthreads: int = 0):
+    """The oracle on a random sample of output columns; nthreads = 0 uses
+    every host core."""
     import oracle
     rng = np.random.default_rng(seed)
     cols = np.sort(rng.choice(A.ncols, ncols_sample, replace=False))
     t0 = time.perf_counter()
-    r = oracle.spgemm(A, A, cols=cols)
+    r = oracle.spgemm(A, A, cols=cols, nthreads=nthreads)
     dt = time.perf_counter() - t0
     products = int(r["flops"].sum())
-    return {"value": 2.0 * products / dt / 1e9, "unit": "GFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
+    return {"value": 2.0 * products / dt / 1e9, "unit": "GFLOP/s", "cores": nthreads or oracle.max_threads(),
+            "kind": "oracle",
             "sample": f"{ncols_sample} random output columns (seed {seed}) of the f64 run: {products} products, "
                       f"{dt:.2f} s", "seconds": dt, "products": products}
 
@@ -366,6 +369,8 @@ def main(argv=None):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = time_oracle(A, CPU_SAMPLE_COLS, seed=0)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        one = time_oracle(A, CPU_SAMPLE_COLS // 16, seed=1, nthreads=1)
+        line["cpu_baseline"]["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
 
     if not args.no_e2e:
         try:
