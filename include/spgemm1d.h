@@ -156,7 +156,9 @@ void spgemm_default_options(spg_options *opt);
  * Algorithm 2).  Reads A and B, allocates and owns the plan's workspace.
  * Synchronises the stream a few times (to size the workspace).
  * Errors: SPG_INVALID_ARGUMENT (null, P < 1, b < 1, A.ncols != B.nrows,
- * bad type codes, mismatched A/B value types), SPG_INVALID_INPUT,
+ * bad type codes, mismatched A/B value types, an output mask with fewer than
+ * ceil(nrows(A) / 32) words per column, mask_complement not 0 or 1, or a mask
+ * with learned sizing), SPG_INVALID_INPUT,
  * SPG_UNSUPPORTED (m, k, n or the gathered column count >= 2^31),
  * SPG_OUT_OF_MEMORY, SPG_CUDA_ERROR.  On error *out is NULL.
  */
@@ -175,7 +177,8 @@ spg_status spgemm_symbolic(spg_plan *plan, void *C_colptr, int64_t *nnzC);
  * spgemm_symbolic (int64, n + 1), C->rowidx room for nnzC entries of the
  * inputs' idx_type and C->vals room for nnzC doubles (double inputs) or int64
  * (integer inputs).  C's size fields and type codes are set by this call.
- * Asynchronous (stream-ordered).
+ * The first call for a plan synchronises the stream once (the sizes of the
+ * light columns' bins are read back); otherwise stream-ordered.
  */
 spg_status spgemm_numeric(spg_plan *plan, spg_csc *C);
 
