@@ -390,13 +390,15 @@ spg_status spgemm_count_noalloc(const spg_csc *A, const spg_csc *B, int64_t *nnz
  * the call returns.  stats (host, may be NULL): the volumes a distributed run
  * with process i owning column block i of A, B and C would move.  Synchronises
  * the stream.  Errors: SPG_INVALID_ARGUMENT (NULL pointers, A.ncols != B.nrows,
- * P < 1), SPG_UNSUPPORTED (int32 row ids of A with 2^31 or more non-empty
+ * P < 1, options carrying a mask), SPG_UNSUPPORTED (int32 row ids of A with 2^31 or more non-empty
  * (i, j) pairs), and those of spgemm_1d_multiply.
  */
 /* ---------------------------------------------------------------------------
  * Batched betweenness centrality (Section 3.2: Brandes' algorithm for a batch
  * of sources, multi-source BFS forward search and backward sweep, each level
- * one column 1D SpGEMM).  A: n x n device CSC of an unweighted graph, column v
+ * one masked column 1D SpGEMM: the forward product keeps the (vertex, source)
+ * pairs not yet visited, the backward product the pairs of the level above).
+ * A: n x n device CSC of an unweighted graph, column v
  * listing the neighbours of v (values ignored; symmetric for an undirected
  * graph).  sources: s device int32 vertex ids (one frontier column each).
  * opt: as for spgemm_1d_multiply (P, b, stream, allocator).  bc: n device
@@ -406,8 +408,8 @@ spg_status spgemm_count_noalloc(const spg_csc *A, const spg_csc *B, int64_t *nnz
  * level_cap levels.  stats (host, may be NULL).  Intermediate frontiers live
  * in memory from opt->alloc and are released before the call returns.
  * Synchronises the stream.  Errors: SPG_INVALID_ARGUMENT (NULL pointers,
- * non-square A, s < 0, a source outside [0, n)), and those of
- * spgemm_1d_multiply.
+ * non-square A, s < 0, a source outside [0, n), options carrying a mask), and
+ * those of spgemm_1d_multiply.
  */
 typedef struct {
     int64_t levels;            /* BFS levels, the sources' own level included */
