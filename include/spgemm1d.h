@@ -68,6 +68,9 @@ typedef enum { SPG_SIZING_EXACT = 0, SPG_SIZING_LEARNED = 1 } spg_sizing;
  * (Section 3.2 count as the weight: bound_i is the smallest j whose preceding
  * columns hold at least i/P of all flops). */
 typedef enum { SPG_SPLIT_UNIFORM = 0, SPG_SPLIT_FLOPS = 1 } spg_split;
+/* The (add, multiply) pair of the product.  This build computes the ordinary
+ * (+, x): doubles, or wrapping 64-bit integers (see the result contract). */
+typedef enum { SPG_SEMIRING_PLUS_TIMES = 0 } spg_semiring;
 
 /* One CSC matrix.  colptr has ncols + 1 entries of ptr_type; rowidx has nnz
  * entries of idx_type; vals has nnz entries of val_type.  All device memory,
@@ -117,7 +120,7 @@ typedef struct {
     const uint32_t *mask;
     int64_t mask_words;     /* words per column of mask, >= ceil(nrows(A) / 32) */
     int32_t mask_complement; /* 0: keep rows whose bit is set; 1: keep rows whose bit is clear */
-    int32_t reserved2;
+    int32_t semiring;       /* spg_semiring (0 = PLUS_TIMES, the only one; others give SPG_UNSUPPORTED) */
 } spg_options;
 
 /* Counters of one plan (filled progressively by plan, symbolic and numeric). */
@@ -159,6 +162,7 @@ void spgemm_default_options(spg_options *opt);
  * bad type codes, mismatched A/B value types, an output mask with fewer than
  * ceil(nrows(A) / 32) words per column, mask_complement not 0 or 1, or a mask
  * with learned sizing), SPG_INVALID_INPUT,
+ * SPG_UNSUPPORTED (a semiring other than SPG_SEMIRING_PLUS_TIMES),
  * SPG_UNSUPPORTED (m, k, n or the gathered column count >= 2^31),
  * SPG_OUT_OF_MEMORY, SPG_CUDA_ERROR.  On error *out is NULL.
  */

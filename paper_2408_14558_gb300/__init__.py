@@ -32,6 +32,7 @@ SPG_IDX_I32, SPG_IDX_I64 = 0, 1
 SPG_VAL_F64, SPG_VAL_I32, SPG_VAL_I64 = 0, 1, 2
 SPG_SIZING_EXACT, SPG_SIZING_LEARNED = 0, 1
 SPG_SPLIT_UNIFORM, SPG_SPLIT_FLOPS = 0, 1
+SPG_SEMIRING_PLUS_TIMES = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_INPUT", 3: "OUT_OF_MEMORY",
                 4: "CUDA_ERROR", 5: "TIMEOUT", 6: "UNSUPPORTED", 7: "OVERFLOW_RECOMPUTED"}
 
@@ -60,7 +61,7 @@ class spg_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p), ("model", ctypes.c_void_p),
                 ("learned_slack", ctypes.c_double), ("mask", ctypes.c_void_p), ("mask_words", ctypes.c_int64),
-                ("mask_complement", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("mask_complement", ctypes.c_int32), ("semiring", ctypes.c_int32)]
 
 
 class spg_stats(ctypes.Structure):

@@ -1084,6 +1084,10 @@ extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_
         set_error("unknown sizing mode %d", opt->sizing);
         return SPG_INVALID_ARGUMENT;
     }
+    if (opt->semiring != SPG_SEMIRING_PLUS_TIMES) {
+        set_error("semiring %d: this build computes (+, x) only", opt->semiring);
+        return SPG_UNSUPPORTED;
+    }
     if (A->nrows >= INT32_MAX || A->ncols >= INT32_MAX || B->ncols >= INT32_MAX) {
         set_error("m, k and n must be < 2^31 - 1");
         return SPG_UNSUPPORTED;

@@ -247,3 +247,16 @@ def test_host_csc_marshalling():
     E = synth.CSC(3, 2, np.zeros(3, np.int64), np.zeros(0, np.int32), np.zeros(0))
     d = g._host_csc(E)
     assert d.nnz == 0 and d.rowidx is None and d.vals is None
+
+
+def test_semiring_other_than_plus_times_is_unsupported(lib):
+    import paper_2408_14558_gb300 as g
+    A = g.spg_csc(4, 5, 0, 0, 0, 0, 0, 1, None, None)
+    B = g.spg_csc(5, 3, 0, 0, 0, 0, 0, 1, None, None)
+    o = g.spg_options()
+    lib.spgemm_default_options(ctypes.byref(o))
+    assert o.semiring == g.SPG_SEMIRING_PLUS_TIMES
+    o.semiring = 1
+    h = ctypes.c_void_p()
+    assert lib.spgemm_plan(ctypes.byref(A), ctypes.byref(B), ctypes.byref(o), ctypes.byref(h)) == g.SPG_UNSUPPORTED
+    assert "semiring" in g.spgemm_last_error() and not h.value
