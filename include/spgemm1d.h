@@ -369,7 +369,9 @@ spg_status spgemm_plan_labels(const spg_plan *plan, float *y);
  *     order them on one stream;
  *   - the first call on a device looks up the array's address with that
  *     device current (cudaGetSymbolAddress); make that first call before any
- *     stream capture on the device.
+ *     stream capture on the device.  The address is kept for the life of the
+ *     process, so a cudaDeviceReset of that device between calls is not
+ *     supported.
  * Inputs must be canonical (no validation pass: that would need memory for a
  * flag).  Asynchronous on `stream` (a cudaStream_t; NULL = legacy stream).
  * Errors: SPG_INVALID_ARGUMENT, SPG_UNSUPPORTED, SPG_CUDA_ERROR.
@@ -472,6 +474,59 @@ typedef void (*spg_host_free_fn)(void *ptr, size_t bytes, void *ctx);
 spg_status spgemm_1d_multiply_host(const spg_csc *A, const spg_csc *B, const spg_options *opt, int32_t chunks,
                                    spg_host_alloc_fn host_alloc, spg_host_free_fn host_free, void *host_ctx,
                                    spg_csc *C);
+
+/* ---------------------------------------------------------------------------
+ * Distributed 1D SpGEMM: the device steps of Algorithm 1 (Section 3.1) when P
+ * processes each own column block i of A, B and C, with Algorithm 2 choosing
+ * what each process fetches.  The transport between processes (NCCL, gloo,
+ * or anything else that moves device buffers) belongs to the caller; the
+ * Python binding's dist1d module drives these calls around collectives.
+ * All three are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ * stream), allocate nothing and take only caller-owned device memory.
+ *
+ * spgemm_dist_fetch_blocks: process i's H_i (the nonzero rows of its B_i,
+ * Table 1) and its chosen fetch blocks: block t = column ids
+ * [t*b, min((t+1)*b, k)) is chosen iff it holds a column c with bit c of H_i
+ * set and A_colptr[c+1] > A_colptr[c] (D~_i = H_i AND D, Algorithm 1;
+ * Algorithm 2 with fixed-width groups).
+ *   B:        process i's local block (k x n_i, rows = global column ids of A);
+ *             only its row ids are read.
+ *   A_colptr: k + 1 int64, the GLOBAL column pointers of A (the per-owner
+ *             column counts after an allgather, scanned).
+ *   H:        workspace and output, ceil(k/32) uint32 words (bit c = row c).
+ *   fetch:    output, ceil(k/b) bytes, 1 = chosen.
+ *   bad:      one device int, set to 1 if a row id of B lies outside [0, k)
+ *             (such ids are skipped, never used as an address).
+ * Errors: SPG_INVALID_ARGUMENT (NULL pointers, bad header, b < 1),
+ * SPG_CUDA_ERROR.
+ */
+spg_status spgemm_dist_fetch_blocks(const spg_csc *B, const int64_t *A_colptr, int64_t b, uint32_t *H,
+                                    uint8_t *fetch, int *bad, void *stream);
+/* spgemm_dist_pack: an owner's reply to one requester (the one-sided fetch of
+ * Algorithm 1, here a send buffer): the entries of local columns
+ * [ranges[2r], ranges[2r+1]) of A, range after range, copied to rows_out /
+ * vals_out starting at out_off[r].
+ *   A:        the owner's local columns (its colptr starts at 0), any index
+ *             and value types; the outputs take A's row id and value types.
+ *   ranges:   device, 2*nr int64 (local column ids, lo <= hi <= A.ncols).
+ *   out_off:  device, nr + 1 int64, out_off[r+1] - out_off[r] = the entries of
+ *             range r, out_off[nr] = total.
+ *   bad:      one device int, set to 1 if a range lies outside A or its size
+ *             disagrees with out_off (offending entries are not copied).
+ * Errors: SPG_INVALID_ARGUMENT, SPG_CUDA_ERROR.
+ */
+spg_status spgemm_dist_pack(const spg_csc *A, const int64_t *ranges, const int64_t *out_off, int64_t nr,
+                            int64_t total, void *rows_out, void *vals_out, int *bad, void *stream);
+/* spgemm_dist_fetched_colptr: the requester's side.  The fetched pieces,
+ * received in ascending column order, form the m x k matrix A_f whose column
+ * c equals A(:, c) when c's fetch block was chosen and is empty otherwise;
+ * A_f * B_i = A * B_i because every column of D~_i lies in a chosen block.
+ * This writes A_f's k + 1 int64 column pointers to colptr_out (device) from
+ * the global A_colptr (device, k + 1) and fetch (device, ceil(k/b) bytes).
+ * Errors: SPG_INVALID_ARGUMENT, SPG_CUDA_ERROR.
+ */
+spg_status spgemm_dist_fetched_colptr(const int64_t *A_colptr, const uint8_t *fetch, int64_t k, int64_t b,
+                                      int64_t *colptr_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -142,6 +142,10 @@ class DeviceCSC:
         for t in (self.colptr, self.rowidx, self.vals):
             if not t.is_cuda or not t.is_contiguous():
                 raise ValueError("DeviceCSC arrays must be contiguous CUDA tensors")
+        if self.colptr.numel() < self.ncols + 1 or self.vals.numel() != self.rowidx.numel():
+            raise ValueError(f"DeviceCSC needs ncols + 1 = {self.ncols + 1} column pointers (has "
+                             f"{self.colptr.numel()}) and one value per row id ({self.vals.numel()} values, "
+                             f"{self.rowidx.numel()} row ids)")
         return spg_csc(self.nrows, self.ncols, self.nnz, _IDX[self.colptr.dtype], _IDX[self.rowidx.dtype],
                        _VAL[self.vals.dtype], 0, self.colptr.data_ptr(),
                        self.rowidx.data_ptr() if self.nnz else None, self.vals.data_ptr() if self.nnz else None)
@@ -627,8 +631,19 @@ def spgemm_count_noalloc(A: DeviceCSC, B: DeviceCSC, nnz_out: torch.Tensor | Non
     rows, and calls that overlap on the GPU race (order them on one stream).
     The output array is the caller's (allocated here by torch if not given)."""
     lib = load_library()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for name, M in (("A", A), ("B", B)):
+        for t in (M.colptr, M.rowidx):
+            if t.device != dev:
+                raise ValueError(f"{name} must be on the current device {dev} (the scratch array is looked up "
+                                 f"for the current device), not {t.device}")
     if nnz_out is None:
-        nnz_out = torch.empty(max(B.ncols, 1), dtype=torch.int64, device=B.colptr.device)
+        nnz_out = torch.empty(max(B.ncols, 1), dtype=torch.int64, device=dev)
+    elif (nnz_out.dtype != torch.int64 or nnz_out.device != dev or not nnz_out.is_contiguous()
+          or nnz_out.numel() < B.ncols):
+        raise ValueError(f"nnz_out must be a contiguous int64 tensor on {dev} with at least {B.ncols} entries "
+                         f"(got {nnz_out.dtype}, {nnz_out.device}, {nnz_out.numel()} entries, "
+                         f"contiguous={nnz_out.is_contiguous()})")
     if stream is None:
         stream = torch.cuda.current_stream()
     a, b = A.as_c(), B.as_c()

@@ -19,7 +19,9 @@
 //     give wrong counts; order them on one stream;
 //   * the first call on each device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture on the device.
+//     before any stream capture on the device.  The address is cached for the
+//     life of the process: a cudaDeviceReset of that device between calls is
+//     not supported (the module, and so the array, may move).
 #include <mutex>
 
 #include "spg_internal.cuh"

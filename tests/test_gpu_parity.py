@@ -8,7 +8,7 @@ import torch
 import oracle
 import paper_2408_14558_gb300 as g
 import synth
-from parity import assert_full_parity, assert_sampled_parity, run_gpu
+from parity import assert_full_parity, assert_sampled_parity, check_values, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -261,6 +261,38 @@ def test_rmat_s18_full_size_sampled():
     assert torch.equal(C.rowidx, Ci.rowidx)
     assert torch.equal(C.vals.to(torch.int64), Ci.vals)
     assert int(C.colptr[-1]) <= int(fl.sum())
+
+
+@pytest.mark.parametrize("vals", ["ones", "i64"])
+def test_rmat_s18_complete_against_oracle(vals):
+    """All of the R-MAT scale-18 squaring (P = 16, b = 1024, the bench's launch
+    configuration and plan/symbolic/numeric calls) against the oracle, one
+    column block at a time (Section 3.1: the block partition never changes the
+    result): column pointers and row ids bit-exact, int64 path counts
+    bit-exact, every double within 1e-12 * sum |a_rk * b_kj|."""
+    A = synth.rmat_symmetric(18, 16, seed=0, values=vals)
+    dA = g.to_device(A, ptr_dtype=torch.int32, idx_dtype=torch.int32)
+    plan = g.spgemm_plan(dA, dA, 16, 1024)
+    colptr, nnz = g.spgemm_symbolic(plan)
+    C = g.spgemm_numeric(plan, colptr)
+    g.spgemm_plan_destroy(plan)
+    torch.cuda.synchronize()
+    cp = C.colptr.cpu().numpy()
+    assert cp[0] == 0 and int(cp[-1]) == nnz
+    bounds = oracle.block_bounds(A.ncols, 16)
+    total = 0
+    for i in range(16):
+        c0, c1 = int(bounds[i]), int(bounds[i + 1])
+        ref = oracle.spgemm(A, A, cols=np.arange(c0, c1))
+        assert np.array_equal(cp[c0:c1 + 1] - cp[c0], ref["colptr"]), f"block {i}: column pointers differ"
+        e0, e1 = int(cp[c0]), int(cp[c1])
+        rows = C.rowidx[e0:e1].cpu().numpy()
+        assert np.array_equal(rows, ref["rowidx"].astype(np.int32)), f"block {i}: row ids differ"
+        del rows
+        check_values(C.vals[e0:e1].cpu().numpy(), ref["vals"], ref["absum"], f"block {i} {vals}")
+        total += e1 - e0
+        del ref
+    assert total == nnz == 2958091137
 
 
 def test_galerkin_128():

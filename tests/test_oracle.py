@@ -230,6 +230,59 @@ def test_flop_identity_and_nnz_bound():
         assert np.array_equal(f["nnzb"], np.diff(B.colptr))
 
 
+def _features_by_loop(A, B):
+    """flops_j, nnz(B(:,j)), max and mean nnz(A(:,k)) over the stored k of
+    B(:,j), by a plain Python loop over B's columns reading A's column counts."""
+    acount = np.diff(np.asarray(A.colptr, dtype=np.int64))
+    fl, nb, mx, mean = [], [], [], []
+    for j in range(B.ncols):
+        ks = [int(k) for k in B.rowidx[B.colptr[j]:B.colptr[j + 1]]]
+        lens = [int(acount[k]) for k in ks]
+        fl.append(sum(lens))
+        nb.append(len(ks))
+        mx.append(max(lens) if lens else 0)
+        mean.append(sum(lens) / len(lens) if lens else 0.0)
+    return np.array(fl), np.array(nb), np.array(mx), np.array(mean)
+
+
+def test_features_against_direct_loop():
+    """Section 3.2 features of every output column (flops, nnz(B(:,j)), max and
+    mean nnz of the contributing A columns) equal a plain loop, on random inputs
+    and on hand-built columns: an empty column, a column whose largest A column
+    comes last, one whose largest comes first, and one that only touches an
+    empty column of A (max 0, not the maximum over B's values or over all A)."""
+    rng = np.random.default_rng(17)
+    cases = [(synth.random_sparse(80, 60, 0.08, rng, values="i32"),
+              synth.random_sparse(60, 90, 0.06, rng, values="i32")) for _ in range(3)]
+    # A: column k has k % 5 entries (column 0, 5, 10 empty); its values are
+    # large so that a max over values, not counts, would differ.
+    dA = np.zeros((12, 12))
+    for k in range(12):
+        dA[: k % 5, k] = 100.0 + k
+    # B's columns: empty; rows {0, 1, 2, 4} (largest A column, 4 entries, last);
+    # rows {9, 1} stored ascending as {1, 9} (largest = column 9, 4 entries, last);
+    # rows {4, 6} (largest first); row {5} (an empty A column); all of A's columns.
+    dB = np.zeros((12, 5))
+    for j, ks in enumerate([[], [0, 1, 2, 4], [1, 9], [4, 6], [5]]):
+        for k in ks:
+            dB[k, j] = 7.0
+    A_hand, B_hand = synth.from_dense(dA), synth.from_dense(dB)
+    cases.append((A_hand, B_hand))
+    for A, B in cases:
+        f = oracle.features(A, B)
+        fl, nb, mx, mean = _features_by_loop(A, B)
+        assert np.array_equal(f["flops"], fl)
+        assert np.array_equal(f["nnzb"], nb)
+        assert np.array_equal(f["maxa"], mx)
+        assert np.allclose(f["meana"], mean, rtol=0, atol=1e-12)
+    f = oracle.features(A_hand, B_hand)
+    assert f["maxa"].tolist() == [0, 4, 4, 4, 0]
+    assert f["flops"].tolist() == [0, 0 + 1 + 2 + 4, 1 + 4, 4 + 1, 0]
+    # a sub-range of columns gives the same rows of the table
+    g = oracle.features(A_hand, B_hand, 1, 4)
+    assert g["maxa"].tolist() == [4, 4, 4]
+
+
 def test_pattern_matches_scipy_all_ones_product():
     """With all-ones values nothing cancels, so the oracle's pattern equals the
     pattern of scipy's product (a library routine)."""
