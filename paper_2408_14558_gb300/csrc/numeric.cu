@@ -120,6 +120,49 @@ __global__ void k_num_headers(int64_t nitems, const int32_t *__restrict__ num_re
     }
 }
 
+// Shared-memory accumulator of a numeric item: cap + 1 slots (the last one a
+// dump slot).  Doubles use the native atomic add of a double.  Wrapping int64
+// sums are kept as two 32-bit halves in separate arrays: a 64-bit add is a
+// 32-bit atomic add on the low half that returns the old low word, from which
+// the carry out of the low half follows exactly; the high half then receives
+// the value's high word plus that carry (skipped when zero, the common case
+// for small non-negative values).  Every update is thus exact modulo 2^64 in
+// any order, and 32-bit shared atomics run several times faster than 64-bit
+// ones on this GPU.
+template <typename Acc>
+struct HeavyAcc;
+template <>
+struct HeavyAcc<double> {
+    double *a;
+    static constexpr size_t bytes_per_slot = 8;
+    __device__ __forceinline__ HeavyAcc(void *base, int) : a((double *)base) {}
+    __device__ __forceinline__ void zero(int i) const { a[i] = 0.0; }
+    __device__ __forceinline__ void add(int i, double v) const { atomicAdd(a + i, v); }
+    __device__ __forceinline__ double get(int i) const { return a[i]; }
+    __device__ __forceinline__ int32_t *scratch32() const { return (int32_t *)a; }
+};
+template <>
+struct HeavyAcc<long long> {
+    uint32_t *lo, *hi;
+    static constexpr size_t bytes_per_slot = 8;
+    __device__ __forceinline__ HeavyAcc(void *base, int slots) : lo((uint32_t *)base), hi((uint32_t *)base + slots) {}
+    __device__ __forceinline__ void zero(int i) const {
+        lo[i] = 0u;
+        hi[i] = 0u;
+    }
+    __device__ __forceinline__ void add(int i, long long v) const {
+        const unsigned long long u = (unsigned long long)v;
+        const uint32_t vlo = (uint32_t)u, vhi = (uint32_t)(u >> 32);
+        const uint32_t old = atomicAdd(lo + i, vlo);
+        const uint32_t h = vhi + ((uint32_t)(old + vlo) < old ? 1u : 0u);
+        if (h) atomicAdd(hi + i, h);
+    }
+    __device__ __forceinline__ long long get(int i) const {
+        return (long long)(((unsigned long long)hi[i] << 32) | (unsigned long long)lo[i]);
+    }
+    __device__ __forceinline__ int32_t *scratch32() const { return (int32_t *)lo; }
+};
+
 // One CTA per numeric item: records [r0, r0 + nr) of one heavy column (base
 // slabs t0 .. t0 + nr - 1) holding cnt <= cap entries of C.  The symbolic
 // bitmaps of the records give every present row its rank (pre[word] + popc of
@@ -138,8 +181,9 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RW = R >> 5;
     CtaBatch<Acc> &sb = *(CtaBatch<Acc> *)smem_raw;
-    Acc *acc = (Acc *)(smem_raw + ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15));
-    uint2 *bp = (uint2 *)(acc + cap + 1);  // (bitmap word, exclusive prefix of popcounts)
+    unsigned char *acc_raw = smem_raw + ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15);
+    const HeavyAcc<Acc> acc(acc_raw, cap + 1);
+    uint2 *bp = (uint2 *)(acc_raw + HeavyAcc<Acc>::bytes_per_slot * (size_t)(cap + 1));  // (bitmap word, prefix)
     __shared__ int wsum[33];
     __shared__ int bad_sh;
     __shared__ long long claim;
@@ -179,7 +223,7 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
         if (cnt == h.cnt && cnt <= cap) {
             // (the first barrier of cta_products orders the zeroing before
             // every product)
-            for (int i = tid; i < cnt; i += blockDim.x) acc[i] = Acc(0);
+            for (int i = tid; i < cnt; i += blockDim.x) acc.zero(i);
             const int wbase = t0 * RW;
             bool miss = false;
             cta_products<true, SPG_NUM_UNROLL, Acc>(
@@ -192,25 +236,26 @@ __global__ void __launch_bounds__(kBatch, SPG_NUM_MINB)
                     // to the dump slot acc[cap] and is reported
                     const bool hit = (x.x >> sh) & 1u;
                     miss |= !hit && !MASKED;  // a masked product is absent by design
-                    atomic_add_acc(acc + (hit ? (int)(x.y + __popc(x.x & ((1u << sh) - 1u))) : cap), v);
+                    acc.add(hit ? (int)(x.y + __popc(x.x & ((1u << sh) - 1u))) : cap, v);
 #else
                     if constexpr (MASKED) {
-                        if ((x.x >> sh) & 1u) atomic_add_acc(acc + (int)(x.y + __popc(x.x & ((1u << sh) - 1u))), v);
+                        if ((x.x >> sh) & 1u) acc.add((int)(x.y + __popc(x.x & ((1u << sh) - 1u))), v);
                     } else {
                         // the rank of a present row; an absent one would still
                         // land inside [0, cnt] (never outside the accumulator)
-                        atomic_add_acc(acc + (int)(x.y + __popc(x.x & ((1u << sh) - 1u))), v);
+                        acc.add((int)(x.y + __popc(x.x & ((1u << sh) - 1u))), v);
                     }
 #endif
                 });
             if (miss) bad_sh = 1;
             if (tid == 0 && (long long)nxt < nitems) nh = items[nxt];
             // cta_products ends with a barrier: acc is complete
-            for (int i = tid; i < cnt; i += blockDim.x) st_stream(Cval + h.cbase + i, acc[i]);
+            for (int i = tid; i < cnt; i += blockDim.x) st_stream(Cval + h.cbase + i, acc.get(i));
             __syncthreads();
             // the row ids go to shared memory by rank first (over the consumed
-            // values: cnt ints fit in cnt Accs), then to C in one coalesced run
-            int32_t *srow = (int32_t *)acc;
+            // values: cnt ints fit in the first cnt slots), then to C in one
+            // coalesced run
+            int32_t *srow = acc.scratch32();
             for (int w = tid; w < nwords; w += blockDim.x) {
                 uint32_t word = bp[w].x;
                 int pos = (int)bp[w].y;
