@@ -476,6 +476,63 @@ spg_status spgemm_1d_multiply_host(const spg_csc *A, const spg_csc *B, const spg
                                    spg_csc *C);
 
 /* ---------------------------------------------------------------------------
+ * One-launch multiply for small products: C = A * B with B and C cut into P
+ * column blocks (Section 3.1, Algorithm 1: per block H_i, D~_i and the chosen
+ * fetch blocks of b column ids (Algorithm 2), then the symbolic and numeric
+ * passes of the local multiply), every step in ONE cooperative persistent
+ * kernel with grid-wide barriers.  The gather of A~_i is fused into the
+ * product loads (each required column of A is read in place), so C is that of
+ * the column 1D path.  Nothing is read back to the host and nothing is
+ * allocated: the call is two clears and one kernel on `stream`, and can be
+ * captured in a CUDA graph and replayed.
+ *
+ * Table classes (table_log): 8 gives every warp 256 slots and runs 32 warps
+ * per SM, for products whose column bounds min(flops_j, m) are all <= 128; 10
+ * gives 1024 slots and 8 warps per SM, for bounds <= 512.
+ *
+ * spgemm_small_bound: bound[0] = max_j min(flops_j, m), bound[1] = sum_j
+ * min(flops_j, m) (an upper bound of nnz(C), usable as C's capacity), written
+ * to `bound` (device, 2 int64) on `stream`; the caller reads them once to
+ * choose the table class and allocate C.
+ *
+ * spgemm_small_workspace: bytes of device workspace the call needs for these
+ * shapes, P, b and table class (depends on the sizes only, and on the GPU's
+ * SM count).
+ *
+ * spgemm_small_multiply:
+ *   A, B:      device CSC as for spgemm_plan; A's row ids must be int32; A and
+ *              B both doubles, or both integers (int32 widened, int64 wrapping).
+ *   workspace: device, >= spgemm_small_workspace bytes, caller-owned; its
+ *              contents need not be preserved between calls.
+ *   C_colptr:  device, n + 1 int64 (written even when C does not fit);
+ *   C_rowidx, C_vals: device, `capacity` int32 row ids and `capacity` values
+ *              (double, or int64 for integer inputs).
+ *   result:    device, 8 int64 written by the kernel: [0] nnz(C), [1] status
+ *              (0, or the spg_status of the first failure: SPG_OUT_OF_MEMORY
+ *              when nnz(C) > capacity (no rows written), SPG_UNSUPPORTED when a
+ *              column's bound min(flops_j, m) exceeds the table class's
+ *              limit (128 or 512), SPG_INVALID_INPUT
+ *              for a row id of B outside A's columns, SPG_TIMEOUT when a grid
+ *              barrier wait exceeded timeout_ns, SPG_CUDA_ERROR for an
+ *              internal inconsistency), [2] products, [3] sum of |H_i|,
+ *              [4] sum of |D~_i|, [5] nonzeros of the A~_i, [6] nonzeros of
+ *              the chosen fetch blocks, [7] chosen fetch blocks.
+ *   timeout_ns: limit of each grid-barrier wait (the CTAs of a cooperative
+ *              launch are co-resident, so it only guards against faults).
+ * Host-side errors (returned): SPG_INVALID_ARGUMENT (NULL pointers, bad
+ * header, P < 1, b < 1, dimension mismatch, mixed value kinds, workspace too
+ * small, table_log not 8 or 10), SPG_UNSUPPORTED (int64 row ids of A),
+ * SPG_CUDA_ERROR (launch).
+ * Inputs are not validated beyond the row ids of B.
+ */
+spg_status spgemm_small_bound(const spg_csc *A, const spg_csc *B, int64_t *bound, void *stream);
+spg_status spgemm_small_workspace(const spg_csc *A, const spg_csc *B, int32_t P, int64_t b, int32_t table_log,
+                                  size_t *bytes);
+spg_status spgemm_small_multiply(const spg_csc *A, const spg_csc *B, int32_t P, int64_t b, int32_t table_log,
+                                 void *workspace, size_t workspace_bytes, int64_t *C_colptr, int32_t *C_rowidx,
+                                 void *C_vals, int64_t capacity, int64_t *result, int64_t timeout_ns, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Distributed 1D SpGEMM: the device steps of Algorithm 1 (Section 3.1) when P
  * processes each own column block i of A, B and C, with Algorithm 2 choosing
  * what each process fetches.  The transport between processes (NCCL, gloo,

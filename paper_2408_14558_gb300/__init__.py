@@ -652,6 +652,87 @@ def spgemm_count_noalloc(A: DeviceCSC, B: DeviceCSC, nnz_out: torch.Tensor | Non
     return nnz_out[: B.ncols]
 
 
+# ------------------------------------------------- one-launch small multiply
+
+SMALL_RESULT_FIELDS = ("nnzC", "status", "products", "sum_H", "sum_dtilde", "gathered_nnz_exact",
+                       "gathered_nnz_block", "fetch_blocks_chosen")
+
+
+def _small_lib():
+    lib = load_library()
+    if not getattr(lib, "_small_ready", False):
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.spgemm_small_bound.argtypes = [ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc), vp, vp]
+        lib.spgemm_small_workspace.argtypes = [ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc), i32, i64, i32,
+                                               ctypes.POINTER(ctypes.c_size_t)]
+        lib.spgemm_small_multiply.argtypes = [ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc), i32, i64, i32, vp,
+                                              ctypes.c_size_t, vp, vp, vp, i64, vp, i64, vp]
+        for name in ("spgemm_small_bound", "spgemm_small_workspace", "spgemm_small_multiply"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib._small_ready = True
+    return lib
+
+
+class SmallProduct:
+    """Buffers of the one-launch multiply of A * B (spgemm_small_multiply):
+    device workspace, C's arrays with room for `capacity` entries and the
+    8-entry result block, allocated once with torch; `run()` only enqueues the
+    call (two clears and one kernel), so it can be captured in a CUDA graph.
+
+    The set-up reads spgemm_small_bound once (one synchronisation): the
+    largest column bound picks the table class (8 when it is <= 128, else 10),
+    and their sum is C's default capacity.  table_log forces a class."""
+
+    def __init__(self, A: DeviceCSC, B: DeviceCSC, P=1, b=1024, capacity=None, timeout_ns=1_000_000_000,
+                 table_log=None):
+        lib = _small_lib()
+        self.A, self.B, self.P, self.b = A, B, int(P), int(b)
+        self._a, self._b = A.as_c(), B.as_c()
+        dev = A.colptr.device
+        bound = torch.zeros(2, dtype=torch.int64, device=dev)
+        _check(lib.spgemm_small_bound(ctypes.byref(self._a), ctypes.byref(self._b), bound.data_ptr(),
+                                      _stream_ptr(None)))
+        self.max_bound, self.nnz_bound = (int(x) for x in bound.cpu())
+        self.table_log = int(table_log) if table_log is not None else (8 if self.max_bound <= 128 else 10)
+        nbytes = ctypes.c_size_t()
+        _check(lib.spgemm_small_workspace(ctypes.byref(self._a), ctypes.byref(self._b), self.P, self.b,
+                                          self.table_log, ctypes.byref(nbytes)))
+        self.capacity = int(self.nnz_bound if capacity is None else capacity)
+        self.workspace = torch.empty(max(int(nbytes.value), 1), dtype=torch.uint8, device=dev)
+        val_dt = torch.float64 if A.vals.dtype == torch.float64 else torch.int64
+        self.colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=dev)
+        self.rowidx = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=dev)
+        self.vals = torch.empty(max(self.capacity, 1), dtype=val_dt, device=dev)
+        self.result = torch.zeros(len(SMALL_RESULT_FIELDS), dtype=torch.int64, device=dev)
+        self.timeout_ns = int(timeout_ns)
+
+    def run(self, stream=None):
+        """Enqueue C = A * B on `stream` (torch's current stream by default)."""
+        _check(_small_lib().spgemm_small_multiply(
+            ctypes.byref(self._a), ctypes.byref(self._b), self.P, self.b, self.table_log, self.workspace.data_ptr(),
+            self.workspace.numel(), self.colptr.data_ptr(), self.rowidx.data_ptr(), self.vals.data_ptr(),
+            self.capacity, self.result.data_ptr(), self.timeout_ns, _stream_ptr(stream)))
+        return self
+
+    def stats(self) -> dict:
+        """The result block (synchronises with the device)."""
+        return dict(zip(SMALL_RESULT_FIELDS, (int(x) for x in self.result.cpu())))
+
+    def C(self) -> DeviceCSC:
+        """C after the call (synchronises; raises SpgError on a device-side failure)."""
+        st = self.stats()
+        if st["status"]:
+            raise SpgError(st["status"], f"one-launch multiply failed on the device (nnz(C) = {st['nnzC']}, "
+                                         f"capacity {self.capacity})")
+        n = st["nnzC"]
+        return DeviceCSC(self.A.nrows, self.B.ncols, self.colptr, self.rowidx[:n], self.vals[:n])
+
+
+def spgemm_small_multiply(A: DeviceCSC, B: DeviceCSC, P=1, b=1024, capacity=None, stream=None) -> DeviceCSC:
+    """One call of the one-launch multiply (buffers allocated for this call)."""
+    return SmallProduct(A, B, P, b, capacity).run(stream).C()
+
+
 # ------------------------------------------------------ learned nnz sizing
 
 SPG_MODEL_NPARAMS = 1249

@@ -240,4 +240,47 @@ __device__ __forceinline__ void warp_sort_pairs(int *keys, Acc *vals, int n, int
     }
 }
 
+// Shared-memory accumulator of a heavy item (slots addressed by rank or by
+// row).  Doubles use the native atomic add of a double.  Wrapping int64
+// sums are kept as two 32-bit halves in separate arrays: a 64-bit add is a
+// 32-bit atomic add on the low half that returns the old low word, from which
+// the carry out of the low half follows exactly; the high half then receives
+// the value's high word plus that carry (skipped when zero, the common case
+// for small non-negative values).  Every update is thus exact modulo 2^64 in
+// any order, and 32-bit shared atomics run several times faster than 64-bit
+// ones on this GPU.
+template <typename Acc>
+struct HeavyAcc;
+template <>
+struct HeavyAcc<double> {
+    double *a;
+    static constexpr size_t bytes_per_slot = 8;
+    __device__ __forceinline__ HeavyAcc(void *base, int) : a((double *)base) {}
+    __device__ __forceinline__ void zero(int i) const { a[i] = 0.0; }
+    __device__ __forceinline__ void add(int i, double v) const { atomicAdd(a + i, v); }
+    __device__ __forceinline__ double get(int i) const { return a[i]; }
+    __device__ __forceinline__ int32_t *scratch32() const { return (int32_t *)a; }
+};
+template <>
+struct HeavyAcc<long long> {
+    uint32_t *lo, *hi;
+    static constexpr size_t bytes_per_slot = 8;
+    __device__ __forceinline__ HeavyAcc(void *base, int slots) : lo((uint32_t *)base), hi((uint32_t *)base + slots) {}
+    __device__ __forceinline__ void zero(int i) const {
+        lo[i] = 0u;
+        hi[i] = 0u;
+    }
+    __device__ __forceinline__ void add(int i, long long v) const {
+        const unsigned long long u = (unsigned long long)v;
+        const uint32_t vlo = (uint32_t)u, vhi = (uint32_t)(u >> 32);
+        const uint32_t old = atomicAdd(lo + i, vlo);
+        const uint32_t h = vhi + ((uint32_t)(old + vlo) < old ? 1u : 0u);
+        if (h) atomicAdd(hi + i, h);
+    }
+    __device__ __forceinline__ long long get(int i) const {
+        return (long long)(((unsigned long long)hi[i] << 32) | (unsigned long long)lo[i]);
+    }
+    __device__ __forceinline__ int32_t *scratch32() const { return (int32_t *)lo; }
+};
+
 }  // namespace spg

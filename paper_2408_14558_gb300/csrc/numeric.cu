@@ -169,49 +169,6 @@ __device__ __forceinline__ int cta_load_scan_bitmap(const uint32_t *__restrict__
     return total;
 }
 
-// Shared-memory accumulator of a numeric item: cap + 1 slots (the last one a
-// dump slot).  Doubles use the native atomic add of a double.  Wrapping int64
-// sums are kept as two 32-bit halves in separate arrays: a 64-bit add is a
-// 32-bit atomic add on the low half that returns the old low word, from which
-// the carry out of the low half follows exactly; the high half then receives
-// the value's high word plus that carry (skipped when zero, the common case
-// for small non-negative values).  Every update is thus exact modulo 2^64 in
-// any order, and 32-bit shared atomics run several times faster than 64-bit
-// ones on this GPU.
-template <typename Acc>
-struct HeavyAcc;
-template <>
-struct HeavyAcc<double> {
-    double *a;
-    static constexpr size_t bytes_per_slot = 8;
-    __device__ __forceinline__ HeavyAcc(void *base, int) : a((double *)base) {}
-    __device__ __forceinline__ void zero(int i) const { a[i] = 0.0; }
-    __device__ __forceinline__ void add(int i, double v) const { atomicAdd(a + i, v); }
-    __device__ __forceinline__ double get(int i) const { return a[i]; }
-    __device__ __forceinline__ int32_t *scratch32() const { return (int32_t *)a; }
-};
-template <>
-struct HeavyAcc<long long> {
-    uint32_t *lo, *hi;
-    static constexpr size_t bytes_per_slot = 8;
-    __device__ __forceinline__ HeavyAcc(void *base, int slots) : lo((uint32_t *)base), hi((uint32_t *)base + slots) {}
-    __device__ __forceinline__ void zero(int i) const {
-        lo[i] = 0u;
-        hi[i] = 0u;
-    }
-    __device__ __forceinline__ void add(int i, long long v) const {
-        const unsigned long long u = (unsigned long long)v;
-        const uint32_t vlo = (uint32_t)u, vhi = (uint32_t)(u >> 32);
-        const uint32_t old = atomicAdd(lo + i, vlo);
-        const uint32_t h = vhi + ((uint32_t)(old + vlo) < old ? 1u : 0u);
-        if (h) atomicAdd(hi + i, h);
-    }
-    __device__ __forceinline__ long long get(int i) const {
-        return (long long)(((unsigned long long)hi[i] << 32) | (unsigned long long)lo[i]);
-    }
-    __device__ __forceinline__ int32_t *scratch32() const { return (int32_t *)lo; }
-};
-
 // One CTA per numeric item: records [r0, r0 + nr) of one heavy column (base
 // slabs t0 .. t0 + nr - 1) holding cnt <= cap entries of C.  The symbolic
 // bitmaps of the records give every present row its rank (pre[word] + popc of
@@ -435,6 +392,7 @@ spg_status prepare_numeric(spg_plan *p) {
 }
 
 spg_status run_numeric(spg_plan *p, spg_csc *C) {
+    spg::PhaseRange nvtx_range("numeric");
     cudaStream_t st = p->st;
     const int64_t n = p->n;
     spg_status s0 = prepare_numeric(p);
