@@ -322,13 +322,14 @@ __global__ void __launch_bounds__(kBatch)
                   Acc *__restrict__ tval, unsigned long long *next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaBatch<Acc> &sb = *(CtaBatch<Acc> *)smem_raw;
-    Acc *acc = (Acc *)(smem_raw + ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15));
-    uint32_t *bits = (uint32_t *)(acc + kFusedRows);
+    unsigned char *acc_raw = smem_raw + ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15);
+    const HeavyAcc<Acc> acc(acc_raw, kFusedRows);  // dense: slot = row within the item
+    uint32_t *bits = (uint32_t *)(acc_raw + HeavyAcc<Acc>::bytes_per_slot * kFusedRows);
     int *pre = (int *)(bits + kFusedRows / 32);
     __shared__ int wsum[33];
     __shared__ long long pos_sh, claim;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = threadIdx.x; i < kFusedRows; i += blockDim.x) acc[i] = Acc(0);
+    for (int i = threadIdx.x; i < kFusedRows; i += blockDim.x) acc.zero(i);
     const int RW = R >> 5;
     for (int64_t it = cta_claim(next, &claim); it < nitems; it = cta_claim(next, &claim)) {
         const int r0 = it_rec0[it], nr = it_nrec[it];
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(kBatch)
             [&](int r, Acc v) {
                 const int lr = (int)(r - rbase);
                 set_bit_shared(bits + (lr >> 5), 1u << (lr & 31));
-                atomic_add_acc(acc + lr, v);
+                acc.add(lr, v);
             });
         const int cnt = cta_scan_popc1(bits, pre, nwords, wsum);
         if (threadIdx.x == 0) {
@@ -377,9 +378,9 @@ __global__ void __launch_bounds__(kBatch)
             if (pos >= 0) {
                 const int64_t o = base + pre[w] + __popc(word & ((1u << lane) - 1u));
                 st_stream(trow + o, (OutIdx)(rbase + lr));
-                st_stream(tval + o, acc[lr]);
+                st_stream(tval + o, acc.get(lr));
             }
-            acc[lr] = Acc(0);
+            acc.zero(lr);
         }
     }
 }
