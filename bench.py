@@ -51,6 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the learned-vs-exact and batched-vs-sequential comparisons of the headline line")
     ap.add_argument("--out-dir", default=os.path.join(tempfile.gettempdir(), "spgemm1d_bench"),
                     help="where the clock samples and the tuning cache are written")
     ap.add_argument("--workload", default="rmat18",
@@ -203,26 +205,39 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- roofline
 
-def _source_digest():
+PROFILE_SCALE = 16     # the ncu capture of the dominant kernel is taken on this R-MAT scale
+
+
+def kernel_source_digest():
+    """Digest of the sources of the heavy numeric kernel (its own file and the
+    headers it includes): a traffic figure taken from an older build is not
+    reported."""
     h = hashlib.sha256()
-    for name in ("numeric.cu", "symbolic.cu", "spg_internal.cuh", "cta_products.cuh", "block_ops.cuh", "plan.cu"):
+    for name in ("numeric.cu", "spg_internal.cuh", "cta_products.cuh", "block_ops.cuh"):
         with open(os.path.join(ROOT, "paper_2408_14558_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, scale: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    if there is none or the sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_rmat_s{scale}.md")
+def profiled_traffic(kernel: str, alg_bytes_per_launch: float):
+    """DRAM bytes per launch of `kernel` at the bench's scale, from the
+    committed ncu summary of a scale-16 capture (one kernel, two launches):
+    its measured read + write bytes scaled by the ratio of algorithmic bytes
+    (traffic grows with the work: C dominates both).  None when there is no
+    summary or the kernel's sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_rmat_s{PROFILE_SCALE}.md")
     if not os.path.exists(path):
-        return None
+        return None, None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    a = re.search(r"algorithmic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     d = re.search(r"source_digest:\s*([0-9a-f]+)", txt)
-    if not m or not d or d.group(1) != _source_digest():
-        return None
-    return float(m.group(1))
+    if not m or not a or not d or d.group(1) != kernel_source_digest():
+        return None, None
+    t, alg = float(m.group(1)), float(a.group(1))
+    return t * alg_bytes_per_launch / alg, {"captured_scale": PROFILE_SCALE, "captured_traffic_per_launch": t,
+                                           "captured_algorithmic_bytes_per_launch": alg,
+                                           "summary": os.path.relpath(path, ROOT)}
 
 
 def kernel_bytes(group: str, st: dict) -> float:
@@ -331,6 +346,8 @@ def main(argv=None):
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
     kernel_name = {"num_heavy": "k_num_heavy", "num_light": "k_num_light", "sym_heavy": "k_sym_heavy",
                    "sym_light": "k_sym_light", "gather": "k_gather_copy"}[dom]
+    traffic, traffic_basis = (profiled_traffic(kernel_name, dom_bytes / 2) if kernel_name == "k_num_heavy"
+                              else (None, None))
     comp = sum(compulsory_bytes(st) for st in stats[0])
     path_gbs = comp / (ms_per_step / 1e3) / 1e9
     launches = sum(st["kernel_launches"] for sts in stats for st in sts)
@@ -348,7 +365,8 @@ def main(argv=None):
             "vs_baseline": None, "dtype": "f64+int64", "data": "synthetic",
             "config": workload_config(args.rmat_scale, stats[0][0]["products"], stats[0][0]["nnzC"]),
             "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(kernel_name, args.rmat_scale),
+                         "frac": achieved / peak, "traffic": traffic, "traffic_basis": traffic_basis,
+                         "algorithmic_bytes_per_launch": dom_bytes / 2,
                          "algorithmic_bytes_per_step": dom_bytes, "ms_per_step": dom_ms,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
             "path_roofline": {"compulsory_bytes_per_step": comp, "achieved": path_gbs, "frac": path_gbs / peak,
@@ -372,6 +390,9 @@ def main(argv=None):
         one = time_oracle(A, CPU_SAMPLE_COLS // 16, seed=1, nthreads=1)
         line["cpu_baseline"]["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
 
+    if rank == 0 and world == 1 and not args.no_compare and args.rmat_scale == RMAT_SCALE:
+        line.update(run_comparisons(args, torch, g))
+
     if not args.no_e2e:
         try:
             line["e2e"] = run_e2e(g, torch, A, Ai, max(1, min(args.steps, 3)), world, products_step,
@@ -386,6 +407,43 @@ def main(argv=None):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def run_comparisons(args, torch, g):
+    """The two comparisons the metric names, each on its own workload and with
+    its own clock record: learned nnz sizing against the exact two-pass
+    multiply (C = A*A^T, 100,000 x 2^20 lognormal/Zipf rows, int64) and one
+    persistent graph launch of 512 uneven products against 512 sequential
+    multiplies.  Both check that the faster form gives the same C."""
+    import argparse
+    import bench_workloads as bw
+    import synth
+    sub = argparse.Namespace(steps=3, warmup=1, out_dir=args.out_dir, no_cpu_baseline=True)
+    out = {}
+    try:
+        sim = bw.run_similarity(sub, torch, g, synth, emit=False)
+        keys = ("exact_ms", "learned_ms", "learned_speedup", "exact_gflops", "learned_gflops", "recompute_rate",
+                "recomputed_columns", "capacity_over_nnz", "learned_equals_exact", "clocks", "steps")
+        out["learned_vs_exact"] = dict({k: sim.get(k) for k in keys}, workload=sim["config"]["workload"],
+                                       products=sim["config"]["products"], nnzC=sim["config"]["nnzC"],
+                                       timing="median of the timed steps, CUDA events, L2 flushed before each")
+    except (RuntimeError, MemoryError) as ex:
+        out["learned_vs_exact"] = {"error": str(ex).splitlines()[0][:300]}
+    torch.cuda.empty_cache()
+    try:
+        bat = bw.run_batched(sub, torch, g, synth, emit=False)
+        keys = ("ms_per_step", "sequential_ms", "speedup_vs_sequential", "value", "sequential_gflops",
+                "rows_equal_sequential", "max_abs_value_diff_vs_sequential", "generation_s", "clocks", "steps")
+        b = {k: bat.get(k) for k in keys}
+        b["batched_ms"] = b.pop("ms_per_step")
+        b["batched_gflops"] = b.pop("value")
+        out["batched_vs_sequential"] = dict(b, workload=bat["config"]["workload"],
+                                            products=bat["config"]["products"], tuned=bat["config"]["tuned"],
+                                            timing="median of the timed steps, CUDA events, L2 flushed before each")
+    except (RuntimeError, MemoryError) as ex:
+        out["batched_vs_sequential"] = {"error": str(ex).splitlines()[0][:300]}
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(g, torch, A, Ai, steps, world, products_step, nnzc):

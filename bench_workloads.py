@@ -36,18 +36,46 @@ BATCH_SAMPLE = 32             # instances of the batched workload the oracle com
 BC_SAMPLE_SOURCES = 2         # sources of the betweenness batch the oracle computes
 
 
+# nvidia-smi clock records of the timed regions since the last line was emitted
+_CLOCKS = []
+
+
+def _merged_clocks():
+    """One clock record for the timed regions of a line: the median of the
+    regions' median SM clocks, the highest maximum, every throttle reason seen."""
+    recs = [c for c in _CLOCKS if c]
+    _CLOCKS.clear()
+    if not recs:
+        return None
+    return {"sm_mhz": statistics.median(c["sm_mhz"] for c in recs), "sm_max_mhz": max(c["sm_max_mhz"] for c in recs),
+            "samples": sum(c["samples"] for c in recs), "reasons": sorted({r for c in recs for r in c["reasons"]}),
+            "regions": len(recs)}
+
+
 def _emit(line):
+    if "clocks" not in line:
+        line["clocks"] = _merged_clocks()
     print(json.dumps(line), flush=True)
 
 
-def _timer(torch):
+def _timer(torch, out_dir=None):
+    import bench
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
+    out_dir = out_dir or os.path.join(os.environ.get("TMPDIR", "/tmp"), "spgemm1d_bench")
 
     def timed(fn, steps, warmup):
-        for _ in range(warmup):
+        # clocks are sampled every 200 ms from the start of the warm-up, which
+        # is extended (never the timed steps) until the GPU has been busy with
+        # this workload for at least 0.6 s, so that short regions get samples
+        clk = bench.ClockSampler(torch.cuda.current_device(), out_dir)
+        clk.start()
+        t0 = time.perf_counter()
+        w = 0
+        while w < warmup or time.perf_counter() - t0 < 0.6:
             fn()
-        torch.cuda.synchronize()
+            torch.cuda.synchronize()
+            w += 1
         out = []
         for s in range(steps):
             flush.fill_(s)
@@ -57,6 +85,7 @@ def _timer(torch):
             e1.record(stream)
             e1.synchronize()
             out.append((e0.elapsed_time(e1), r))
+        _CLOCKS.append(clk.stop())
         return out
     return timed
 
@@ -152,6 +181,50 @@ def _graph_replay_ms(torch, g, dA, dB, P, b, reps=200):
     return e0.elapsed_time(e1) / reps
 
 
+def _one_launch(torch, g, dA, dB, P, b, reps=50):
+    """The one-launch multiply (spgemm_small_multiply) captured in a CUDA graph:
+    the median time of single replays, each after a 256 MiB write that evicts
+    L2 (cold), and the mean of back-to-back replays (warm: the product fits in
+    L2).  Returns (cold ms, warm ms, the SmallProduct)."""
+    import bench
+    sp = g.SmallProduct(dA, dB, P, b)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            sp.run(s)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            sp.run(s)
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+        clk = bench.ClockSampler(torch.cuda.current_device(), os.path.join(os.environ.get("TMPDIR", "/tmp"),
+                                                                             "spgemm1d_bench"))
+        clk.start()
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 0.6:       # warm-up long enough for clock samples
+            graph.replay()
+            torch.cuda.synchronize()
+        cold = []
+        for r in range(reps):
+            flush.fill_(r)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            graph.replay()
+            e1.record(s)
+            e1.synchronize()
+            cold.append(e0.elapsed_time(e1))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(200):
+            graph.replay()
+        e1.record(s)
+        e1.synchronize()
+        _CLOCKS.append(clk.stop())
+    st = sp.stats()
+    assert st["status"] == 0
+    return statistics.median(cold), e0.elapsed_time(e1) / 200, sp, st
+
+
 def run_uniform(args, torch, g, synth):
     A = synth.uniform_columns(8192, 8, seed=0)
     dA = g.to_device(A, ptr_dtype=torch.int32, idx_dtype=torch.int32)
@@ -167,18 +240,35 @@ def run_uniform(args, torch, g, synth):
     res = timed(step, max(args.steps, 20), max(args.warmup, 5))
     ms = statistics.median(t for t, _ in res)
     st = res[0][1]
+    cold_ms, warm_ms, sp, sst = _one_launch(torch, g, dA, dA, 4, 256)
+    import bench
     import oracle
+    comp = bench.compulsory_bytes(st)
+    peak, src = bench.measured_peak_hbm()
+    ach = comp / (cold_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_small_multiply (one cooperative launch, graph replay)", "achieved": ach,
+            "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "algorithmic_bytes_per_step": comp, "ms_per_step": cold_ms,
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+            "note": "bytes: B, the gathered A columns and C once; time: one graph replay after an L2 flush"}
     cpu = _cpu_baseline(args, lambda: oracle.spgemm(A, A)["flops"].sum(), "the whole product")
-    _emit(_base("uniform8192_d8_P4_b256", "C=A·A GFLOP/s", 2 * st["products"] / (ms / 1e3) / 1e9, ms, len(res),
-                max(args.warmup, 5), "f64", {"products": st["products"], "nnzC": st["nnzC"]},
-                roofline=_roofline(_column_groups([st]), _KERNELS,
-                                   note="the multiply is launch bound: compare phase_ms with ms_per_step"),
-                cpu_baseline=cpu,
-                phase_ms={k: st["ms_" + k] for k in ("plan", "symbolic", "numeric")},
-                gpu_launches=st["kernel_launches"], l2="flushed before every timed step",
-                graph_replay_ms=_graph_replay_ms(torch, g, dA, dA, 4, 256),
-                note="median over steps; the whole multiply is latency bound (tens of kernel launches, host syncs); "
-                     "graph_replay_ms = one captured value refresh + numeric pass (same patterns), L2-resident"))
+    _emit(_base("uniform8192_d8_P4_b256", "C=A·A GFLOP/s (one-launch multiply, CUDA graph replay)",
+                2 * st["products"] / (cold_ms / 1e3) / 1e9, cold_ms, 50, 3, "f64",
+                {"products": st["products"], "nnzC": st["nnzC"]},
+                roofline=roof, cpu_baseline=cpu, gpu_launches=1,
+                one_launch={"cold_ms": cold_ms, "warm_ms": warm_ms, "warm_gflops": 2 * st["products"] / (warm_ms / 1e3) / 1e9,
+                            "nnzC": sst["nnzC"], "sum_dtilde": sst["sum_dtilde"],
+                            "fetch_blocks_chosen": sst["fetch_blocks_chosen"]},
+                multi_launch={"ms": ms, "gflops": 2 * st["products"] / (ms / 1e3) / 1e9, "steps": len(res),
+                              "phase_ms": {k: st["ms_" + k] for k in ("plan", "symbolic", "numeric")},
+                              "gpu_launches": st["kernel_launches"],
+                              "roofline": _roofline(_column_groups([st]), _KERNELS)},
+                graph_replay_refresh_ms=_graph_replay_ms(torch, g, dA, dA, 4, 256),
+                l2="value: median of 50 single graph replays, each after a 256 MiB write that evicts L2; "
+                   "warm_ms: mean of 200 back-to-back replays (the whole product fits in L2)",
+                note="value = spgemm_small_multiply (plan, symbolic and numeric in one cooperative kernel, two "
+                     "clears, no host read-back) replayed from a CUDA graph; multi_launch = the plan / symbolic / "
+                     "numeric calls of the column 1D path (host read-backs of sizes between phases)"))
 
 
 def run_galerkin(args, torch, g, synth):
@@ -222,7 +312,7 @@ def run_galerkin(args, torch, g, synth):
                 note="graph_replay_ms = one captured value refresh + numeric pass of A*P_agg (same patterns)"))
 
 
-def run_similarity(args, torch, g, synth):
+def run_similarity(args, torch, g, synth, emit=True):
     from paper_2408_14558_gb300 import learned
     A, At = synth.lognormal_zipf_rows(seed=0)
     dA = g.to_device(A, ptr_dtype=torch.int64, idx_dtype=torch.int32)
@@ -276,13 +366,27 @@ def run_similarity(args, torch, g, synth):
     extra["cpu_baseline"] = _cpu_baseline(args, lambda: oracle.spgemm(A, At, cols=cols)["flops"].sum(),
                                           f"{SIM_SAMPLE_COLS} random columns of C (seed 0)")
     extra["gpu_launches"] = sum(s_["kernel_launches"] for s_ in (le[0][1] if model is not None else ex[0][1]))
-    _emit(_base("similarity_AAt_100k_x_1M_lognormal_zipf", "C=A·Aᵀ GFLOP/s (learned sizing; exact alongside)",
-                value, ms, max(args.steps, 2), max(args.warmup, 1), "int64",
-                {"nnzA": A.nnz, "products": prods, "nnzC": nnzc, "column_chunks": chunks, "P": P, "b": 1024},
-                **extra))
+    if model is not None:
+        # outside the timed region: the learned C equals the exact C, chunk by chunk
+        same = True
+        for B in parts:
+            Ce, _ = g.spgemm_1d_multiply(dA, B, P=P // chunks, b=1024)
+            Cl, _ = g.spgemm_1d_multiply(dA, B, P=P // chunks, b=1024, sizing=g.SPG_SIZING_LEARNED, model=model)
+            same = same and torch.equal(Ce.colptr, Cl.colptr) and torch.equal(Ce.rowidx, Cl.rowidx) and \
+                torch.equal(Ce.vals, Cl.vals)
+            del Ce, Cl
+        extra["learned_equals_exact"] = bool(same)
+    line = _base("similarity_AAt_100k_x_1M_lognormal_zipf", "C=A·Aᵀ GFLOP/s (learned sizing; exact alongside)",
+                 value, ms, max(args.steps, 2), max(args.warmup, 1), "int64",
+                 {"nnzA": A.nnz, "products": prods, "nnzC": nnzc, "column_chunks": chunks, "P": P, "b": 1024},
+                 **extra)
+    if not emit:
+        line["clocks"] = _merged_clocks()
+        return line
+    _emit(line)
 
 
-def run_batched(args, torch, g, synth):
+def run_batched(args, torch, g, synth, emit=True):
     t0 = time.time()
     pairs = synth.batch_instances(512, 1000, 200000, seed=0)
     gen_s = time.time() - t0
@@ -318,19 +422,36 @@ def run_batched(args, torch, g, synth):
     ms_s = statistics.median(t for t, _ in seq)
     prods, nbytes = seq[0][1]
     info = g.spgemm_batch_info(batch)
+    # outside the timed region: every instance of the batch against its own
+    # sequential multiply (rows exactly; doubles to rounding, reported as the
+    # largest absolute difference: the order of the additions differs)
+    rows_same, worst = True, 0.0
+    for i, (A, B) in enumerate(zip(As, Bs)):
+        Cs, _ = g.spgemm_1d_multiply(A, B, P=1, b=1024)
+        bcp, brow, bval = g.spgemm_batch_result(batch, i)
+        rows_same = rows_same and torch.equal(Cs.colptr, bcp.to(Cs.colptr.dtype)) and \
+            torch.equal(Cs.rowidx, brow.to(Cs.rowidx.dtype))
+        if rows_same and Cs.vals.numel():
+            worst = max(worst, float((Cs.vals - bval).abs().max()))
+        del Cs, bcp, brow, bval
     import oracle
     pick = np.sort(np.random.default_rng(0).choice(len(pairs), BATCH_SAMPLE, replace=False))
     cpu = _cpu_baseline(args, lambda: sum(int(oracle.spgemm(*pairs[i])["flops"].sum()) for i in pick),
                         f"{BATCH_SAMPLE} random instances (seed 0)")
     roof = _roofline({"batch": (nbytes, ms_b)}, {"batch": "k_batch_persistent (3 table classes, one graph)"},
                      note="bytes: every instance's B, gathered A columns and C once; time: the whole graph launch")
-    _emit(_base("batched_512_er_rmat_n1e3_2e5_d4_32", "batched C_j=A_j·B_j GFLOP/s (one persistent graph launch)",
+    line = _base("batched_512_er_rmat_n1e3_2e5_d4_32", "batched C_j=A_j·B_j GFLOP/s (one persistent graph launch)",
                 2 * prods / (ms_b / 1e3) / 1e9, ms_b, len(res), max(args.warmup, 2), "f64",
                 {"instances": 512, "products": prods, "tuned": tune, "tasks": info["tasks"],
                  "grid": info["grid"], "pool_entries": info["pool_entries"]},
                 roofline=roof, cpu_baseline=cpu,
                 sequential_ms=ms_s, sequential_gflops=2 * prods / (ms_s / 1e3) / 1e9, speedup_vs_sequential=ms_s / ms_b,
-                batch_create_ms=create_ms, generation_s=gen_s))
+                batch_create_ms=create_ms, generation_s=gen_s, rows_equal_sequential=bool(rows_same),
+                max_abs_value_diff_vs_sequential=worst)
+    if not emit:
+        line["clocks"] = _merged_clocks()
+        return line
+    _emit(line)
 
 
 def run_galerkin_right(args, torch, g, synth):

@@ -95,8 +95,9 @@ def _distinct_rows(rng, d_per_col: np.ndarray, sampler, max_rounds=500):
     ncols = d_per_col.shape[0]
     cols = np.repeat(np.arange(ncols, dtype=np.int64), d_per_col)
     rows = sampler(cols.shape[0])
-    order = np.lexsort((rows, cols))
-    cols, rows = cols[order], rows[order]
+    # (col, row) order through one int64 key (rows < 2^31, so key = col * 2^31 + row)
+    key = np.sort((cols << 31) | rows)
+    cols, rows = key >> 31, key & ((1 << 31) - 1)
     # Entries of the columns still holding a repeat, as positions in the
     # (col, row)-sorted arrays; a column's entries are contiguous, so re-sorting
     # only those entries keeps the whole array sorted.
@@ -112,8 +113,7 @@ def _distinct_rows(rng, d_per_col: np.ndarray, sampler, max_rounds=500):
         r[dup] = sampler(nd)
         bad = np.isin(c, np.unique(c[dup]))
         idx, c, r = idx[bad], c[bad], r[bad]
-        o = np.lexsort((r, c))
-        rows[idx] = r[o]
+        rows[idx] = np.sort((c << 31) | r) & ((1 << 31) - 1)
     raise RuntimeError("could not draw distinct rows")
 
 
@@ -258,13 +258,14 @@ def random_instance(n: int, d: int, kind: str, rng, m: int | None = None,
     elif kind == "rmat":
         L = max(1, int(math.ceil(math.log2(m))))
         w = (np.int64(1) << np.arange(L - 1, -1, -1, dtype=np.int64))
+        wf = w.astype(np.float64)
 
         def sampler(s):
             out = np.empty(s, dtype=np.int64)
             todo = np.arange(s)
             while todo.size:
                 bits = rng.random((todo.size, L)) < 0.24
-                r = bits.astype(np.int64) @ w
+                r = (bits.astype(np.float64) @ wf).astype(np.int64)   # exact: sums of powers of 2 below 2^53
                 ok = r < m
                 out[todo[ok]] = r[ok]
                 todo = todo[~ok]
