@@ -34,6 +34,7 @@ extern "C" spg_status spgemm_last_multiply_stats(spg_stats *st) {
 }
 
 extern "C" spg_status spgemm_symbolic(spg_plan *p, void *C_colptr, int64_t *nnzC) {
+    spg::PhaseRange nvtx_range("spgemm_symbolic");
     clear_error();
     if (!p || !nnzC) {
         set_error("plan and nnzC must not be NULL");
@@ -54,6 +55,7 @@ extern "C" spg_status spgemm_symbolic(spg_plan *p, void *C_colptr, int64_t *nnzC
 }
 
 extern "C" spg_status spgemm_numeric(spg_plan *p, spg_csc *C) {
+    spg::PhaseRange nvtx_range("spgemm_numeric");
     clear_error();
     if (!p || !C) {
         set_error("plan and C must not be NULL");
@@ -124,6 +126,7 @@ extern "C" spg_status spgemm_plan_capture(spg_plan *p, spg_csc *C) {
 }
 
 extern "C" spg_status spgemm_plan_replay(spg_plan *p) {
+    spg::PhaseRange nvtx_range("spgemm_plan_replay");
     clear_error();
     if (!p || !p->graph_exec) {
         set_error("no captured graph on this plan (spgemm_plan_capture)");
@@ -180,6 +183,7 @@ void *spg::alloc_user(const spg_options *opt, size_t bytes) {
 }
 
 extern "C" spg_status spgemm_1d_multiply(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C) {
+    spg::PhaseRange nvtx_range("spgemm_1d_multiply");
     clear_error();
     if (!C || !opt) {
         set_error("C and options must not be NULL");

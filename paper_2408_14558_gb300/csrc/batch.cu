@@ -523,6 +523,7 @@ extern "C" spg_status spgemm_batch_create(int32_t count, const spg_csc *A, const
 }
 
 extern "C" spg_status spgemm_batch_execute(spg_batch *b, void *stream) {
+    spg::PhaseRange nvtx_range("spgemm_batch_execute");
     clear_error();
     if (!b) {
         set_error("batch is NULL");

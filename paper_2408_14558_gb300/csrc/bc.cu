@@ -151,6 +151,7 @@ spg_status multiply_f64(const spg_csc *A, const spg_csc *B, const spg_options *o
 
 extern "C" spg_status spgemm_bc_batch(const spg_csc *A, const int32_t *sources, int32_t s, const spg_options *opt,
                                       double *bc, int64_t *level_nnz, int32_t level_cap, spg_bc_stats *stats) {
+    spg::PhaseRange nvtx_range("spgemm_bc_batch");
     clear_error();
     if (!A || !opt || !bc || (s > 0 && !sources) || s < 0 || level_cap < 0) {
         set_error("A, options, bc and (for s > 0) sources must not be NULL; s >= 0");

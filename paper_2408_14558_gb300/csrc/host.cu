@@ -131,6 +131,7 @@ void add_stats(spg_stats &S, const spg_stats &t) {
 extern "C" spg_status spgemm_1d_multiply_host(const spg_csc *A, const spg_csc *B, const spg_options *opt,
                                               int32_t chunks, spg_host_alloc_fn host_alloc,
                                               spg_host_free_fn host_free, void *host_ctx, spg_csc *C) {
+    spg::PhaseRange nvtx_range("spgemm_1d_multiply_host");
     clear_error();
     if (!opt || !C || !host_alloc || chunks < 1) {
         set_error("options, C and host_alloc must not be NULL; chunks >= 1");

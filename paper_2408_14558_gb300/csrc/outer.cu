@@ -174,6 +174,7 @@ static void free_csc(const spg_options *o, spg_csc &M) {
 
 extern "C" spg_status spgemm_outer_multiply(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_csc *C,
                                             spg_outer_stats *stats) {
+    spg::PhaseRange nvtx_range("spgemm_outer_multiply");
     clear_error();
     if (!A || !B || !opt || !C) {
         set_error("A, B, options and C must not be NULL");

@@ -1050,6 +1050,7 @@ extern "C" void spgemm_default_options(spg_options *opt) {
 }
 
 extern "C" spg_status spgemm_plan(const spg_csc *A, const spg_csc *B, const spg_options *opt, spg_plan **out) {
+    spg::PhaseRange nvtx_range("spgemm_plan");
     clear_error();
     if (!out) {
         set_error("out is NULL");

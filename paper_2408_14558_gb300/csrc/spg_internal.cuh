@@ -24,9 +24,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "spgemm1d.h"
 
 namespace spg {
+
+// A named NVTX range for the lifetime of the object: every entry point and
+// every phase of a multiply shows up by name in a profiler's timeline (the
+// calls do nothing unless a tool is attached).
+struct PhaseRange {
+    explicit PhaseRange(const char *name) { nvtxRangePushA(name); }
+    ~PhaseRange() { nvtxRangePop(); }
+    PhaseRange(const PhaseRange &) = delete;
+    PhaseRange &operator=(const PhaseRange &) = delete;
+};
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kEmptyKey = -1;

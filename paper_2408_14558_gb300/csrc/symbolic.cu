@@ -190,6 +190,7 @@ static spg_status launch_sym_light(spg_plan *p, const int32_t *list, int64_t cnt
 }
 
 static spg_status symbolic_heavy(spg_plan *p) {
+    spg::PhaseRange nvtx_range("symbolic: heavy columns");
     cudaStream_t st = p->st;
     const int threads = kBatch;
     size_t smem = sizeof(CtaBatch<long long>) + sizeof(uint32_t) * (size_t)kSymMaxWords;
@@ -230,6 +231,7 @@ static spg_status symbolic_heavy(spg_plan *p) {
 }
 
 spg_status run_symbolic(spg_plan *p) {
+    spg::PhaseRange nvtx_range("symbolic");
     cudaStream_t st = p->st;
     const int64_t n = p->n;
     spg_status s = cuda_check(cudaMemsetAsync(p->nnzcol, 0, sizeof(int64_t) * (size_t)(n + 1), st), "memset");
