@@ -20,6 +20,14 @@
 // Output: one pool for all instances; instance i owns [out_base_i,
 // out_base_i + bound_i) where bound_i = sum_j min(flops_j, m_i) (from the
 // bounds pass at creation), of which it uses its nnz.
+// Heavy columns (bound above the largest warp table, 1024) are CTA tasks of
+// two more kernels in the same graph: one before the class kernels counts
+// each such column with a shared row bitmap (kept in a global scratch) and
+// one after them writes it in row windows of up to kHeavyCap entries, the
+// rows' ranks taken from the stored bitmap.  Kernel order in the graph makes
+// every wait of theirs already satisfied: the class kernels find the heavy
+// counts done, and the heavy numeric kernel finds its instances' column
+// pointers published.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -27,6 +35,7 @@
 #include <vector>
 
 #include "block_ops.cuh"
+#include "cta_products.cuh"
 #include "spg_internal.cuh"
 
 namespace spg {
@@ -48,6 +57,16 @@ struct BatchInst {
 struct BatchTask {
     int32_t inst, c0, c1, pad;
 };
+
+// One heavy column: instance, column, and the first word of its row bitmap in
+// the heavy scratch (ceil(m / 32) words).
+struct BatchHeavy {
+    int32_t inst, col;
+    int64_t bits_off;
+};
+constexpr int kHeavyMaxWords = 8192;   // a heavy column's instance has at most 262,144 rows
+constexpr int kHeavyWinWords = 2048;   // rows of one numeric window: <= 65,536
+constexpr int kHeavyCap = 4096;        // entries of one numeric window
 
 constexpr int kBatchMaxLogS = 11;  // per-warp tables of up to 2048 slots
 // Instances are launched in three classes by the table their largest column
@@ -75,7 +94,7 @@ __device__ __forceinline__ long long bval_load<long long>(const void *v, int vt,
 // Per column: flops_j and U_j = min(flops_j, m); per instance: sum of U_j
 // (the output bound) and max U_j (the table size).
 __global__ void k_batch_bounds(const BatchInst *insts, const BatchTask *tasks, int64_t ntasks,
-                               unsigned long long *bound, unsigned int *maxU) {
+                               unsigned long long *bound, unsigned int *maxU, unsigned int *colU) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -95,12 +114,60 @@ __global__ void k_batch_bounds(const BatchInst *insts, const BatchTask *tasks, i
             const long long U = min(fl, (long long)in.m);
             sum += (unsigned long long)U;
             mx = max(mx, (unsigned int)min(U, (long long)UINT32_MAX));
+            if (lane == 0) colU[in.col_base + j] = (unsigned int)min(U, (long long)UINT32_MAX);
         }
         if (lane == 0) {
             atomicAdd(bound + tk.inst, sum);
             atomicMax(maxU + tk.inst, mx);
         }
     }
+}
+
+// Column pointers of instance `inst` from its per-column counts (one warp),
+// then its ready flag.
+__device__ __forceinline__ void instance_scan(const BatchInst &in, int inst, const int64_t *nnz, int64_t *colptr,
+                                              int *ready, int lane) {
+    const int64_t colb = in.col_base;
+    __threadfence();
+    int64_t run = 0;
+    for (int64_t j0 = 0; j0 < in.n; j0 += 32) {
+        const int64_t j = j0 + lane;
+        const int64_t v = j < in.n ? *(volatile const int64_t *)(nnz + colb + j) : 0;
+        int64_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t x = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += x;
+        }
+        if (j < in.n) colptr[colb + inst + j] = run + inc - v;
+        run += __shfl_sync(kFull, inc, 31);
+    }
+    if (lane == 0) {
+        colptr[colb + inst + in.n] = run;
+        __threadfence();
+        atomicExch(ready + inst, 1);
+    }
+    __syncwarp();
+}
+
+// Bounded wait (one thread) for an instance's ready flag; false on timeout.
+__device__ __forceinline__ bool wait_ready(const int *ready, int inst, int stall_inst, long long timeout_ns, int *err) {
+    const int *flag = ready + inst;
+    int never = 0;
+    if (inst == stall_inst) flag = &never;  // failure test: a flag nothing sets
+    unsigned long long start = 0, now = 0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(start));
+    while (true) {
+        if (*(volatile const int *)flag == 1) {
+            __threadfence();
+            return true;
+        }
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        if ((long long)(now - start) > timeout_ns) break;
+        __nanosleep(256);
+    }
+    atomicOr(err, kBatchErrTimeout);
+    return false;
 }
 
 __device__ __forceinline__ int log_table(long long U) {
@@ -113,7 +180,8 @@ template <int LOGS_MAX, typename Acc, typename OutIdx>
 __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const BatchTask *__restrict__ tasks,
                                    int64_t ntasks, unsigned long long *head, int *sym_done, int *ready,
                                    int64_t *nnz, int64_t *colptr, OutIdx *__restrict__ out_row,
-                                   Acc *__restrict__ out_val, int *err, long long timeout_ns, int stall_inst) {
+                                   Acc *__restrict__ out_val, int *err, long long timeout_ns, int stall_inst,
+                                   const uint8_t *__restrict__ heavy_col) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int S_MAX = 1 << LOGS_MAX;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -141,6 +209,7 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
         };
         if (!numeric) {
             for (int j = tk.c0; j < tk.c1; j++) {
+                if (heavy_col[colb + j]) continue;  // counted by the heavy kernel
                 const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
                 // the class's largest table: every column's bound min(flops, m)
                 // is <= S_MAX / 2, so it needs no pass of its own
@@ -168,53 +237,16 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
                 mine = atomicAdd(sym_done + tk.inst, 1) + 1 == in.ntask ? 1 : 0;
             }
             mine = __shfl_sync(kFull, mine, 0);
-            if (mine) {
-                __threadfence();
-                int64_t run = 0;
-                for (int64_t j0 = 0; j0 < in.n; j0 += 32) {
-                    const int64_t j = j0 + lane;
-                    const int64_t v = j < in.n ? *(volatile int64_t *)(nnz + colb + j) : 0;
-                    int64_t inc = v;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int64_t x = __shfl_up_sync(kFull, inc, o);
-                        if (lane >= o) inc += x;
-                    }
-                    if (j < in.n) colptr[colb + tk.inst + j] = run + inc - v;
-                    run += __shfl_sync(kFull, inc, 31);
-                }
-                if (lane == 0) {
-                    colptr[colb + tk.inst + in.n] = run;
-                    __threadfence();
-                    atomicExch(ready + tk.inst, 1);
-                }
-                __syncwarp();
-            }
+            if (mine) instance_scan(in, tk.inst, nnz, colptr, ready, lane);
         } else {
             // wait, bounded, for the instance's column pointers
             int ok = 0;
-            if (lane == 0) {
-                const int *flag = ready + tk.inst;
-                int never = 0;
-                if (tk.inst == stall_inst) flag = &never;  // failure test: a flag nothing sets
-                unsigned long long start = 0, now = 0;
-                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(start));
-                while (true) {
-                    if (*(volatile const int *)flag == 1) {
-                        ok = 1;
-                        break;
-                    }
-                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-                    if ((long long)(now - start) > timeout_ns) break;
-                    __nanosleep(256);
-                }
-                if (!ok) atomicOr(err, kBatchErrTimeout);
-                __threadfence();
-            }
+            if (lane == 0) ok = wait_ready(ready, tk.inst, stall_inst, timeout_ns, err) ? 1 : 0;
             ok = __shfl_sync(kFull, ok, 0);
             if (!ok) break;
             const int64_t *cp = colptr + colb + tk.inst;
             for (int j = tk.c0; j < tk.c1; j++) {
+                if (heavy_col[colb + j]) continue;  // written by the heavy kernel
                 const int64_t base = in.out_base + cp[j];
                 const int64_t want = cp[j + 1] - cp[j];
                 const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
@@ -270,6 +302,134 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
     }
 }
 
+// Heavy columns of the batch, one CTA per column task (claimed from `head`);
+// the instance's A is read in place (its values in the accumulation type).
+// PHASE 0: every product sets its row's bit in a shared bitmap of the
+// instance's rows; the bitmap goes to the scratch, its popcount to nnz, and
+// the instance's symbolic-task counter advances (its last task scans).
+// PHASE 1: after the instance's ready flag, the column in row windows of at
+// most kHeavyWinWords bitmap words and kHeavyCap entries: the window's words
+// and their popcount prefix give every row its rank, products of rows in the
+// window accumulate at acc[rank], and the window is written in row order.
+template <int PHASE, typename Acc, typename OutIdx>
+__global__ void __launch_bounds__(kBatch)
+    k_batch_heavy(const BatchInst *__restrict__ insts, const BatchHeavy *__restrict__ htasks, int64_t nh,
+                  unsigned long long *head, int *sym_done, int *ready, int64_t *nnz, int64_t *colptr,
+                  uint32_t *__restrict__ scratch, OutIdx *__restrict__ out_row, Acc *__restrict__ out_val, int *err,
+                  long long timeout_ns, int stall_inst) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CtaBatch<Acc> &sb = *(CtaBatch<Acc> *)smem_raw;
+    unsigned char *area = smem_raw + ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15);
+    __shared__ long long claim;
+    __shared__ int ctot[kHeavyWinWords / 32];
+    __shared__ int red[32];
+    __shared__ int cut_sh, flag_sh;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    for (int64_t t = cta_claim(head, &claim); t < nh; t = cta_claim(head, &claim)) {
+        const BatchHeavy hv = htasks[t];
+        const BatchInst in = insts[hv.inst];
+        const int j = hv.col;
+        const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
+        const int nwords = (int)((in.m + 31) / 32);
+        auto seg = [&](int64_t p, long long &st, int &len, Acc &bv) {
+            const int k = in.Brow[p];
+            if ((uint64_t)k < (uint64_t)in.k) {
+                st = ld_ptr(in.Acp, in.acp64, k);
+                len = (int)(ld_ptr(in.Acp, in.acp64, k + 1) - st);
+                if (PHASE == 1) bv = bval_load<Acc>(in.Bval, in.vt, p);
+            }
+        };
+        if (PHASE == 0) {
+            uint32_t *bits = (uint32_t *)area;
+            const SegReg<Acc> first = cta_first_seg<Acc>(p0, p1, seg);
+            for (int w = tid; w < nwords; w += blockDim.x) bits[w] = 0;
+            // (the first barrier of cta_products orders the clearing before every product)
+            cta_products<false, SPG_SYM_UNROLL, Acc>(p0, p1, sb, in.Arow, (const Acc *)nullptr, first, seg,
+                                                     [&](int r, Acc) {
+                                                         if ((uint64_t)r < (uint64_t)in.m)
+                                                             set_bit_shared(bits + (r >> 5), 1u << (r & 31));
+                                                     });
+            int c = 0;
+            uint32_t *dst = scratch + hv.bits_off;
+            for (int w = tid; w < nwords; w += blockDim.x) {
+                const uint32_t x = bits[w];
+                dst[w] = x;
+                c += __popc(x);
+            }
+            c = warp_sum_i(c);
+            if (lane == 0) red[wid] = c;
+            __syncthreads();
+            if (tid == 0) {
+                int tot = 0;
+                for (int w = 0; w < nw; w++) tot += red[w];
+                nnz[in.col_base + j] = tot;
+                __threadfence();
+                flag_sh = atomicAdd(sym_done + hv.inst, 1) + 1 == in.ntask ? 1 : 0;
+            }
+            __syncthreads();
+            if (flag_sh && wid == 0) instance_scan(in, hv.inst, nnz, colptr, ready, lane);
+        } else {
+            if (tid == 0) flag_sh = wait_ready(ready, hv.inst, stall_inst, timeout_ns, err) ? 1 : 0;
+            __syncthreads();
+            if (!flag_sh) return;  // a timeout is recorded; the CTA stops
+            const HeavyAcc<Acc> acc(area, kHeavyCap + 1);
+            uint2 *bp = (uint2 *)(area + HeavyAcc<Acc>::bytes_per_slot * (size_t)(kHeavyCap + 1));
+            const int64_t cbase = in.out_base + colptr[in.col_base + hv.inst + j];
+            const int64_t want = colptr[in.col_base + hv.inst + j + 1] - colptr[in.col_base + hv.inst + j];
+            const uint32_t *src = scratch + hv.bits_off;
+            int64_t done = 0;
+            for (int w0 = 0; w0 < nwords;) {
+                const int nwin = min(kHeavyWinWords, nwords - w0);
+                const int total = cta_load_scan_bitmap(src + w0, bp, nwin, ctot);
+                if (tid == 0) cut_sh = nwin;
+                __syncthreads();
+                if (total > kHeavyCap) {
+                    // the first word that does not fit ends the window
+                    for (int w = tid; w < nwin; w += blockDim.x)
+                        if ((int)bp[w].y + __popc(bp[w].x) > kHeavyCap) atomicMin(&cut_sh, w);
+                    __syncthreads();
+                }
+                const int wcut = cut_sh;
+                const int cnt = wcut < nwin ? (int)bp[wcut].y : total;
+                for (int i = tid; i < cnt; i += blockDim.x) acc.zero(i);
+                const int rlo = w0 * 32, span = wcut * 32;
+                const SegReg<Acc> first = cta_first_seg<Acc>(p0, p1, seg);
+                // (the first barrier of cta_products orders the zeroing before every product)
+                cta_products<true, SPG_NUM_UNROLL, Acc>(
+                    p0, p1, sb, in.Arow, (const Acc *)in.Aval, first, seg, [&](int r, Acc v) {
+                        const int lr = r - rlo;
+                        if ((unsigned)lr < (unsigned)span) {
+                            const uint2 x = bp[lr >> 5];
+                            const uint32_t sh = lr & 31;
+                            if ((x.x >> sh) & 1u) acc.add((int)(x.y + __popc(x.x & ((1u << sh) - 1u))), v);
+                        }
+                    });
+                if (done + cnt <= want) {
+                    for (int i = tid; i < cnt; i += blockDim.x) out_val[cbase + done + i] = acc.get(i);
+                    __syncthreads();
+                    int32_t *srow = acc.scratch32();
+                    for (int w = tid; w < wcut; w += blockDim.x) {
+                        uint32_t word = bp[w].x;
+                        int pos = (int)bp[w].y;
+                        while (word) {
+                            srow[pos++] = rlo + w * 32 + __ffs(word) - 1;
+                            word &= word - 1u;
+                        }
+                    }
+                    __syncthreads();
+                    for (int i = tid; i < cnt; i += blockDim.x) out_row[cbase + done + i] = (OutIdx)srow[i];
+                } else if (tid == 0) {
+                    atomicOr(err, kDevErrInternal);  // never write past the column's room
+                }
+                __syncthreads();
+                done += cnt;
+                w0 += wcut;
+            }
+            if (tid == 0 && done != want) atomicOr(err, kDevErrInternal);
+        }
+    }
+}
+
 }  // namespace spg
 
 struct spg_batch {
@@ -292,6 +452,11 @@ struct spg_batch {
     size_t smem = 0;
     int64_t class_off[spg::kBatchClasses + 1] = {};  // tasks of class c: [class_off[c], class_off[c + 1])
     int sm_count = 0;
+    // heavy columns (CTA tasks)
+    int64_t nheavy = 0;
+    spg::BatchHeavy *htasks = nullptr;
+    uint8_t *heavy_col = nullptr;   // per batch column: 1 = handled by the heavy kernels
+    uint32_t *hscratch = nullptr;   // the heavy columns' row bitmaps
 };
 
 using namespace spg;
@@ -349,8 +514,31 @@ static spg_status batch_launch_class(spg_batch *b, int c) {
     b->smem = std::max(b->smem, smem);
     kern<<<grid, b->warps * 32, smem, b->cap_stream>>>(
         b->insts, b->tasks + t0, nt, b->head + c, b->sym_done, b->ready, b->nnz, b->colptr, (OutIdx *)b->out_row,
-        (Acc *)b->out_val, b->err, b->opt.timeout_ns, b->opt.stall_instance);
+        (Acc *)b->out_val, b->err, b->opt.timeout_ns, b->opt.stall_instance, b->heavy_col);
     return cuda_check(cudaGetLastError(), "batch kernel launch");
+}
+
+// The heavy columns' kernel of one phase (0: counts, 1: values), CTAs claim
+// column tasks from their own counter.
+template <int PHASE, typename Acc, typename OutIdx>
+static spg_status batch_launch_heavy(spg_batch *b) {
+    if (b->nheavy == 0) return SPG_OK;
+    auto kern = k_batch_heavy<PHASE, Acc, OutIdx>;
+    const size_t area = std::max(sizeof(uint32_t) * (size_t)kHeavyMaxWords,
+                                 sizeof(Acc) * (size_t)(kHeavyCap + 1) + sizeof(uint2) * (size_t)kHeavyWinWords);
+    const size_t smem = ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15) + area;
+    spg_status s = cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                              "batch heavy smem");
+    if (s) return s;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBatch, smem);
+    if (occ < 1) occ = 1;
+    const int grid = (int)std::min<int64_t>((int64_t)b->sm_count * occ, b->nheavy);
+    kern<<<grid, kBatch, smem, b->cap_stream>>>(b->insts, b->htasks, b->nheavy, b->head + kBatchClasses + PHASE,
+                                               b->sym_done, b->ready, b->nnz, b->colptr, b->hscratch,
+                                               (OutIdx *)b->out_row, (Acc *)b->out_val, b->err, b->opt.timeout_ns,
+                                               b->opt.stall_instance);
+    return cuda_check(cudaGetLastError(), "batch heavy kernel launch");
 }
 
 // One graph: clear the counters and flags, then the class kernels in turn.
@@ -358,12 +546,17 @@ template <typename Acc, typename OutIdx>
 static spg_status batch_capture(spg_batch *b) {
     spg_status s = cuda_check(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
     if (s) return s;
-    cudaMemsetAsync(b->head, 0, sizeof(unsigned long long) * kBatchClasses, b->cap_stream);
+    cudaMemsetAsync(b->head, 0, sizeof(unsigned long long) * (kBatchClasses + 2), b->cap_stream);
     cudaMemsetAsync(b->sym_done, 0, sizeof(int) * (size_t)b->count * 2 + sizeof(int) * 4, b->cap_stream);
     static_assert(kBatchClasses == 3, "one launch per class below");
-    s = batch_launch_class<kBatchClassLogS[0], Acc, OutIdx>(b, 0);
+    // heavy counts first: the class kernels' last symbolic task of an instance
+    // then scans counts that are all there; heavy values last: their
+    // instances' column pointers are published by then
+    s = batch_launch_heavy<0, Acc, OutIdx>(b);
+    if (!s) s = batch_launch_class<kBatchClassLogS[0], Acc, OutIdx>(b, 0);
     if (!s) s = batch_launch_class<kBatchClassLogS[1], Acc, OutIdx>(b, 1);
     if (!s) s = batch_launch_class<kBatchClassLogS[2], Acc, OutIdx>(b, 2);
+    if (!s) s = batch_launch_heavy<1, Acc, OutIdx>(b);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
     b->graph = g;
@@ -441,7 +634,7 @@ extern "C" spg_status spgemm_batch_create(int32_t count, const spg_csc *A, const
     if (!s) {
         b->insts = (BatchInst *)batch_alloc(b, sizeof(BatchInst) * (size_t)count);
         b->tasks = (BatchTask *)batch_alloc(b, sizeof(BatchTask) * (size_t)b->ntasks);
-        b->head = (unsigned long long *)batch_alloc(b, sizeof(unsigned long long) * kBatchClasses);
+        b->head = (unsigned long long *)batch_alloc(b, sizeof(unsigned long long) * (kBatchClasses + 2));
         b->sym_done = (int *)batch_alloc(b, sizeof(int) * (size_t)count * 2 + sizeof(int) * 4);
         b->nnz = (int64_t *)batch_alloc(b, sizeof(int64_t) * (size_t)(col + 1));
         b->colptr = (int64_t *)batch_alloc(b, sizeof(int64_t) * (size_t)(col + count + 1));
@@ -453,30 +646,65 @@ extern "C" spg_status spgemm_batch_create(int32_t count, const spg_csc *A, const
         s = cuda_check(cudaMemcpy(b->insts, b->hinst.data(), sizeof(BatchInst) * (size_t)count, cudaMemcpyHostToDevice), "insts");
     }
     if (!s) s = cuda_check(cudaMemcpy(b->tasks, htask.data(), sizeof(BatchTask) * htask.size(), cudaMemcpyHostToDevice), "tasks");
-    // bounds pass: output room and table sizes
+    // bounds pass: output room, table sizes and every column's bound
     std::vector<unsigned long long> bound(count);
-    std::vector<unsigned int> maxU(count);
+    std::vector<unsigned int> maxU(count, 0u), colU((size_t)std::max<int64_t>(col, 1));
     if (!s) {
         unsigned long long *db = (unsigned long long *)batch_alloc(b, sizeof(unsigned long long) * (size_t)count);
         unsigned int *dm = (unsigned int *)batch_alloc(b, sizeof(unsigned int) * (size_t)count);
-        if (!db || !dm) s = SPG_OUT_OF_MEMORY;
+        unsigned int *du = (unsigned int *)batch_alloc(b, sizeof(unsigned int) * (size_t)std::max<int64_t>(col, 1));
+        if (!db || !dm || !du) s = SPG_OUT_OF_MEMORY;
         if (!s) {
             cudaMemset(db, 0, sizeof(unsigned long long) * (size_t)count);
             cudaMemset(dm, 0, sizeof(unsigned int) * (size_t)count);
-            k_batch_bounds<<<grid_for(b->ntasks * 32, 256, b->sm_count * 16), 256>>>(b->insts, b->tasks, b->ntasks, db, dm);
+            k_batch_bounds<<<grid_for(b->ntasks * 32, 256, b->sm_count * 16), 256>>>(b->insts, b->tasks, b->ntasks, db,
+                                                                                  dm, du);
             s = cuda_check(cudaGetLastError(), "bounds");
         }
         if (!s) s = cuda_check(cudaMemcpy(bound.data(), db, sizeof(unsigned long long) * (size_t)count, cudaMemcpyDeviceToHost), "bounds");
-        if (!s) s = cuda_check(cudaMemcpy(maxU.data(), dm, sizeof(unsigned int) * (size_t)count, cudaMemcpyDeviceToHost), "bounds");
+        if (!s && col > 0)
+            s = cuda_check(cudaMemcpy(colU.data(), du, sizeof(unsigned int) * (size_t)col, cudaMemcpyDeviceToHost), "bounds");
+    }
+    // heavy columns: bound above the largest warp table; the rest sets the
+    // instance's table class
+    std::vector<BatchHeavy> hheavy;
+    std::vector<uint8_t> hflag((size_t)std::max<int64_t>(col, 1), 0);
+    int64_t hwords = 0;
+    if (!s) {
+        const unsigned int lim = 1u << (kBatchMaxLogS - 1);
+        for (int i = 0; i < count && !s; i++) {
+            const BatchInst &in = b->hinst[i];
+            for (int64_t j = 0; j < in.n; j++) {
+                const unsigned int U = colU[in.col_base + j];
+                if (U <= lim) {
+                    maxU[i] = std::max(maxU[i], U);
+                    continue;
+                }
+                if (in.m > (int64_t)kHeavyMaxWords * 32 || (in.vt == SPG_VAL_I32)) {
+                    set_error("instance %d has a column of up to %u entries: heavy columns need at most %d rows and "
+                              "double or int64 values (use spgemm_1d_multiply for such products)", i, U,
+                              kHeavyMaxWords * 32);
+                    s = SPG_UNSUPPORTED;
+                    break;
+                }
+                hflag[in.col_base + j] = 1;
+                hheavy.push_back({i, (int32_t)j, hwords});
+                hwords += (in.m + 31) / 32;
+                b->hinst[i].ntask++;
+            }
+        }
     }
     if (!s) {
-        unsigned int mx = 0;
-        for (int i = 0; i < count; i++) mx = std::max(mx, maxU[i]);
-        if (mx > (1u << (kBatchMaxLogS - 1))) {
-            set_error("a column of the batch may hold %u entries; the batched path handles <= %d per column "
-                      "(use spgemm_1d_multiply for such products)", mx, 1 << (kBatchMaxLogS - 1));
-            s = SPG_UNSUPPORTED;
-        }
+        b->nheavy = (int64_t)hheavy.size();
+        b->heavy_col = (uint8_t *)batch_alloc(b, (size_t)std::max<int64_t>(col, 1));
+        b->htasks = (BatchHeavy *)batch_alloc(b, sizeof(BatchHeavy) * (size_t)std::max<int64_t>(b->nheavy, 1));
+        b->hscratch = (uint32_t *)batch_alloc(b, sizeof(uint32_t) * (size_t)std::max<int64_t>(hwords, 1));
+        if (!b->heavy_col || !b->htasks || !b->hscratch) s = SPG_OUT_OF_MEMORY;
+        if (!s) s = cuda_check(cudaMemcpy(b->heavy_col, hflag.data(), (size_t)std::max<int64_t>(col, 1),
+                                          cudaMemcpyHostToDevice), "heavy flags");
+        if (!s && b->nheavy)
+            s = cuda_check(cudaMemcpy(b->htasks, hheavy.data(), sizeof(BatchHeavy) * hheavy.size(),
+                                      cudaMemcpyHostToDevice), "heavy tasks");
     }
     if (!s) {
         // the tasks of each class together, instance order kept inside a class

@@ -283,4 +283,53 @@ struct HeavyAcc<long long> {
     __device__ __forceinline__ int32_t *scratch32() const { return (int32_t *)lo; }
 };
 
+// Load a heavy item's bitmap words into bp[].x and their exclusive popcount
+// prefix into bp[].y, returning the total.  Warp w takes 32-word chunks w,
+// w + nw, ...: lanes load consecutive words (coalesced, one word per bank
+// pair) and scan them with shuffles; a second pass adds the chunk offsets
+// (every warp scans the chunk totals itself).  ctot holds one int per chunk
+// (nwords <= 32 * 64).  Ends with a barrier.
+__device__ __forceinline__ int cta_load_scan_bitmap(const uint32_t *__restrict__ src, uint2 *bp, int nwords,
+                                                    int *ctot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nch = (nwords + 31) >> 5;
+    for (int c = wid; c < nch; c += nw) {
+        const int w = (c << 5) + lane;
+        const uint32_t x = w < nwords ? ld_stream(src + w) : 0u;
+        const int pc = __popc(x);
+        int inc = pc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (w < nwords) bp[w] = make_uint2(x, (uint32_t)(inc - pc));
+        if (lane == 31) ctot[c] = inc;
+    }
+    __syncthreads();
+    // exclusive prefix of the chunk totals, each warp for itself (<= 64 chunks)
+    const int t0 = lane < nch ? ctot[lane] : 0, t1 = lane + 32 < nch ? ctot[lane + 32] : 0;
+    int i0 = t0, i1 = t1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(kFull, i0, o), b = __shfl_up_sync(kFull, i1, o);
+        if (lane >= o) {
+            i0 += a;
+            i1 += b;
+        }
+    }
+    const int half = __shfl_sync(kFull, i0, 31);
+    const int total = half + __shfl_sync(kFull, i1, 31);
+    for (int c = wid; c < nch; c += nw) {
+        // offset of chunk c = exclusive prefix at c
+        const int src_lane = c & 31;
+        const int e0 = __shfl_sync(kFull, i0 - t0, src_lane), e1 = __shfl_sync(kFull, i1 - t1, src_lane);
+        const int off = c < 32 ? e0 : half + e1;
+        const int w = (c << 5) + lane;
+        if (w < nwords) bp[w].y += (uint32_t)off;
+    }
+    __syncthreads();
+    return total;
+}
+
 }  // namespace spg

@@ -122,7 +122,8 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
                 // next chunk lies in s or s + 1
                 int sp = sb.pref[s], slen = sb.len[s];
                 int snext = s + 1 < nl ? sb.pref[s + 1] : nch;
-                long long sst = sb.start[s];
+                const int32_t *srp = At_row + sb.start[s];
+                const Acc *svp = NEED_VAL ? At_val + sb.start[s] : nullptr;
                 Acc sbv = NEED_VAL ? sb.bv[s] : Acc(0);
                 for (int c = c0; c < c1; c += U) {
                     int r[U];
@@ -140,16 +141,20 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
                                 s++;
                                 sp = snext;
                                 slen = sb.len[s];
-                                sst = sb.start[s];
-                                if (NEED_VAL) sbv = sb.bv[s];
+                                const long long st2 = sb.start[s];
+                                srp = At_row + st2;
+                                if (NEED_VAL) {
+                                    svp = At_val + st2;
+                                    sbv = sb.bv[s];
+                                }
                                 snext = s + 1 < nl ? sb.pref[s + 1] : nch;
                             }
                             const int off = ((cu - sp) << 5) + lane;
                             if (off < slen) {
                                 ok[u] = true;
-                                r[u] = __ldg(At_row + sst + off);
+                                r[u] = __ldg(srp + off);
                                 if (NEED_VAL) {
-                                    a[u] = __ldg(At_val + sst + off);
+                                    a[u] = __ldg(svp + off);
                                     bu[u] = sbv;
                                 }
                             }

@@ -58,8 +58,46 @@ def test_batch_timeout_is_reported_and_context_survives():
     assert np.array_equal(cp.cpu().numpy(), ref["colptr"])
 
 
-def test_batch_rejects_heavy_columns():
-    A = synth.uniform_columns(3000, 40, seed=1)          # 1600 products per column
+def _columns(M, c0, c1):
+    cp = np.asarray(M.colptr, dtype=np.int64)
+    s, e = int(cp[c0]), int(cp[c1])
+    return synth.CSC(M.nrows, c1 - c0, cp[c0:c1 + 1] - s, np.asarray(M.rowidx[s:e]), np.asarray(M.vals[s:e]))
+
+
+@pytest.mark.parametrize("values", ["f64", "i64"])
+def test_batch_with_heavy_columns_matches_oracle(values):
+    """Instances whose columns exceed the largest warp table (bound > 1024)
+    run as CTA tasks of the same graph: R-MAT column blocks (hub columns among
+    light ones), an instance whose every column is heavy, and light instances,
+    all compared with the oracle, twice (the graph resets its queues)."""
+    pairs = list(synth.batch_instances(6, 300, 6000, seed=4, values=values))
+    R = synth.rmat_symmetric(12, 16, seed=5, values="ones" if values == "f64" else "i64")
+    for c0, c1 in ((0, 700), (700, 2100), (2100, R.ncols)):
+        pairs.append((R, _columns(R, c0, c1)))
+    U = synth.uniform_columns(3000, 40, seed=1, values=values)   # 1600 products per column: all heavy
+    pairs.append((U, U))
+    As = [g.to_device(A) for A, _ in pairs]
+    Bs = [g.to_device(B) for _, B in pairs]
+    fl = [oracle.features(A, B)["flops"] for A, B in pairs]
+    assert any((np.minimum(f, A.nrows) > 1024).any() and (np.minimum(f, A.nrows) <= 1024).any()
+               for f, (A, _) in zip(fl, pairs))
+    batch = g.spgemm_batch_create(As, Bs, task_cols=64, warps_per_cta=8)
+    for rep in range(2):
+        g.spgemm_batch_execute(batch)
+        assert g.spgemm_batch_status(batch) == g.SPG_OK
+        for i, (A, B) in enumerate(pairs):
+            cp, ri, v = g.spgemm_batch_result(batch, i)
+            ref = oracle.spgemm(A, B)
+            assert np.array_equal(cp.cpu().numpy(), ref["colptr"]), (rep, i)
+            assert np.array_equal(ri.cpu().numpy().astype(np.int64), ref["rowidx"]), (rep, i)
+            check_values(v.cpu().numpy(), ref["vals"], ref["absum"], f"instance {i}")
+    g.spgemm_batch_destroy(batch)
+
+
+def test_batch_heavy_limits():
+    """Heavy columns with int32 values (the CTA tasks read A's values in the
+    accumulation type) are refused with SPG_UNSUPPORTED."""
+    A = synth.uniform_columns(3000, 40, seed=1, values="i32")
     dA = g.to_device(A)
     with pytest.raises(g.SpgError) as e:
         g.spgemm_batch_create([dA], [dA])
