@@ -205,7 +205,7 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- roofline
 
-PROFILE_SCALE = 16     # the ncu capture of the dominant kernel is taken on this R-MAT scale
+PROFILE_SCALE = 18     # the ncu capture of the dominant kernel is taken on this R-MAT scale
 
 
 def kernel_source_digest():
@@ -220,11 +220,12 @@ def kernel_source_digest():
 
 
 def profiled_traffic(kernel: str, alg_bytes_per_launch: float):
-    """DRAM bytes per launch of `kernel` at the bench's scale, from the
-    committed ncu summary of a scale-16 capture (one kernel, two launches):
-    its measured read + write bytes scaled by the ratio of algorithmic bytes
-    (traffic grows with the work: C dominates both).  None when there is no
-    summary or the kernel's sources changed since it was taken."""
+    """DRAM bytes per launch of `kernel`, from the committed ncu summary of a
+    capture at the bench's scale (one kernel, two launches, metrics of one
+    ncu pass): its mean read + write bytes, times the ratio of this run's
+    algorithmic bytes to the captured launch's (1 for the same workload).
+    None when there is no summary or the kernel's sources changed since it
+    was taken."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_rmat_s{PROFILE_SCALE}.md")
     if not os.path.exists(path):
         return None, None
@@ -346,8 +347,8 @@ def main(argv=None):
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
     kernel_name = {"num_heavy": "k_num_heavy", "num_light": "k_num_light", "sym_heavy": "k_sym_heavy",
                    "sym_light": "k_sym_light", "gather": "k_gather_copy"}[dom]
-    traffic, traffic_basis = (profiled_traffic(kernel_name, dom_bytes / 2) if kernel_name == "k_num_heavy"
-                              else (None, None))
+    traffic, traffic_basis = (profiled_traffic(kernel_name, dom_bytes / 2)
+                              if kernel_name == "k_num_heavy" and args.rmat_scale == PROFILE_SCALE else (None, None))
     comp = sum(compulsory_bytes(st) for st in stats[0])
     path_gbs = comp / (ms_per_step / 1e3) / 1e9
     launches = sum(st["kernel_launches"] for sts in stats for st in sts)
