@@ -51,6 +51,52 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
+// Hub columns of A: the columns with at least `T` entries get a row bitmap
+// of their own (Wa words, padded to a multiple of 4), so that the heavy
+// symbolic pass ORs a hub's words into an item's bitmap instead of walking
+// the hub's entries one product at a time (the bitmap it builds is the same).
+// In skewed graphs a few hundred such columns carry most of the products.
+__global__ void k_deg_hist(const void *Acp, int ap64, int64_t k, unsigned long long *hist) {
+    __shared__ unsigned int h[64];
+    if (threadIdx.x < 64) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < k; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = ld_ptr(Acp, ap64, c + 1) - ld_ptr(Acp, ap64, c);
+        if (d > 0) atomicAdd(h + (63 - __clzll((unsigned long long)d)), 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 64 && h[threadIdx.x]) atomicAdd(hist + threadIdx.x, (unsigned long long)h[threadIdx.x]);
+}
+
+__global__ void k_hub_index(const void *Acp, int ap64, int64_t k, int64_t T, int32_t *hubidx, int *count) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < k; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = ld_ptr(Acp, ap64, c + 1) - ld_ptr(Acp, ap64, c);
+        hubidx[c] = d >= T ? atomicAdd(count, 1) : -1;
+    }
+}
+
+// Warp per column of A: a hub's rows set their bits (rows outside [0, m) are
+// skipped: validation reports them).
+__global__ void k_hub_bits(const void *Acp, int ap64, const void *Arow, int ai64, int64_t k, int64_t m,
+                           const int32_t *hubidx, int64_t Wa, uint32_t *hubbits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = gw; c < k; c += nw) {
+        const int h = hubidx[c];
+        if (h < 0) continue;
+        const int64_t e0 = ld_ptr(Acp, ap64, c), e1 = ld_ptr(Acp, ap64, c + 1);
+        uint32_t *dst = hubbits + (int64_t)h * Wa;
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int64_t r = ld_ptr(Arow, ai64, e);
+            if ((uint64_t)r < (uint64_t)m) atomicOr(dst + (r >> 5), 1u << (r & 31));
+        }
+    }
+}
+
+// Hub entries one symbolic item may OR instead of walking (the rest walk).
+constexpr int kSymMaxHubs = 512;
+
 // One CTA per symbolic item: records [r0, r0 + nr) of one heavy column, i.e.
 // base slabs t0 .. t0 + nr - 1.  Every product sets its row's bit; then the
 // bitmap of each record and its population count are stored.
@@ -61,18 +107,28 @@ __global__ void SPG_SYM_BOUNDS
                 const int32_t *__restrict__ At_row, const int32_t *__restrict__ split, int T, int R,
                 uint32_t *__restrict__ hbits, int32_t *__restrict__ rec_cnt, unsigned long long *next,
                 const int64_t *__restrict__ flops, const int32_t *__restrict__ win_lo,
-                const int32_t *__restrict__ win_hi, OutMask mask, int64_t mwords_used) {
+                const int32_t *__restrict__ win_hi, OutMask mask, int64_t mwords_used,
+                const int32_t *__restrict__ dtilde, const int32_t *__restrict__ hubidx,
+                const uint4 *__restrict__ hubbits, int64_t Wa4, int hub_min_len) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int RW = R >> 5;
     CtaBatch<long long> &sb = *(CtaBatch<long long> *)smem_raw;
-    uint32_t *bits = (uint32_t *)(smem_raw + sizeof(CtaBatch<long long>));
+    // 16-byte aligned: the hub words are ORed in as uint4
+    uint32_t *bits = (uint32_t *)(smem_raw + ((sizeof(CtaBatch<long long>) + 15) & ~(size_t)15));
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __shared__ long long claim;
+    __shared__ int hubs[kSymMaxHubs];
+    __shared__ int nhub;
+    if (threadIdx.x == 0) nhub = 0;
     for (int64_t it = cta_claim(next, &claim); it < nitems; it = cta_claim(next, &claim)) {
         const int r0 = sym_rec0[it], nr = sym_nrec[it];
         const int j = rec_col[r0], t0 = rec_slab[r0];
         const int nwords = nr * RW;
         const int64_t p0 = ld_ptr(Bcolptr, p64, j), p1 = ld_ptr(Bcolptr, p64, j + 1);
+        // a segment of a hub column of A at least hub_min_len long, and
+        // long enough that ORing the item's words costs less than walking it
+        // (8 x its length >= the item's words), is not walked: the hub's
+        // bitmap words are ORed in after the walk
         auto seg = [&](int64_t p, long long &st, int &len, long long &) {
             int q = Bq[p];
             if (q >= 0) {
@@ -80,6 +136,16 @@ __global__ void SPG_SYM_BOUNDS
                 int a = sp[t0], b = sp[t0 + nr];
                 st = At_colptr[q] + a;
                 len = b - a;
+                if (hubbits && len >= hub_min_len && 8 * (int64_t)len >= nwords) {
+                    const int h = hubidx[dtilde[q]];
+                    if (h >= 0) {
+                        const int pos = atomicAdd(&nhub, 1);
+                        if (pos < kSymMaxHubs) {
+                            hubs[pos] = h;
+                            len = 0;
+                        }
+                    }
+                }
             }
         };
         const SegReg<long long> first = cta_first_seg<long long>(p0, p1, seg);
@@ -97,7 +163,27 @@ __global__ void SPG_SYM_BOUNDS
                 else
                     atomicOr(bits + ((r >> 5) - wbase), 1u << (r & 31));
             });
-        // cta_products ends with a barrier: the bitmap is complete
+        // cta_products ends with a barrier: the walked products are marked;
+        // now the hub segments, each thread ORing the words it owns (the rows
+        // of the item are words [t0 * RW, t0 * RW + nwords) of a hub bitmap;
+        // both are multiples of 4, so whole uint4 words)
+        const int nh = min(nhub, kSymMaxHubs);
+        if (nh > 0) {
+            uint4 *b4 = (uint4 *)bits;
+            const int64_t base4 = (int64_t)t0 * RW / 4;
+            for (int w4 = threadIdx.x; w4 < nwords / 4; w4 += blockDim.x) {
+                uint4 y = b4[w4];
+                for (int hh = 0; hh < nh; hh++) {
+                    const uint4 x = __ldg(hubbits + (int64_t)hubs[hh] * Wa4 + base4 + w4);
+                    y.x |= x.x;
+                    y.y |= x.y;
+                    y.z |= x.z;
+                    y.w |= x.w;
+                }
+                b4[w4] = y;
+            }
+            __syncthreads();
+        }
         if (mask.bits) {
             // keep the rows the output mask admits (words past the last row of
             // C hold no products and have no mask words)
@@ -115,6 +201,8 @@ __global__ void SPG_SYM_BOUNDS
             if (lane == 0) rec_cnt[r0 + rr] = c;
         }
         __syncthreads();
+        // every thread has read nhub; the next claim's barrier publishes the reset
+        if (threadIdx.x == 0) nhub = 0;
     }
 }
 
@@ -189,23 +277,82 @@ static spg_status launch_sym_light(spg_plan *p, const int32_t *list, int64_t cnt
     return cuda_check(cudaGetLastError(), "symbolic light");
 }
 
+// Hub columns of A for the heavy symbolic pass: the threshold is the smallest
+// power of two >= kHubMinDeg whose hubs' bitmaps fit kHubBytes (one
+// histogram read-back).  No hubs: *hubbits stays NULL.
+constexpr int64_t kHubMinDeg = 1024;
+constexpr size_t kHubBytes = size_t(64) << 20;
+
+static spg_status build_hubs(spg_plan *p, int32_t **hubidx, uint4 **hubbits, int64_t *Wa4) {
+    *hubidx = nullptr;
+    *hubbits = nullptr;
+    *Wa4 = 0;
+    const int64_t k = p->k;
+    if (k == 0) return SPG_OK;
+    cudaStream_t st = p->st;
+    const int ap64 = p->A.ptr_type == SPG_IDX_I64;
+    // words of a hub bitmap: every base slab of the heavy items (a multiple of 4)
+    const int64_t Wa = (int64_t)p->T * (p->R / 32);
+    unsigned long long *hist = (unsigned long long *)ws_alloc(p, sizeof(unsigned long long) * 64);
+    int *count = (int *)ws_alloc(p, sizeof(int) * 4);
+    if (!hist || !count) return SPG_OUT_OF_MEMORY;
+    spg_status s = cuda_check(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 64, st), "memset");
+    if (s) return s;
+    launch(p, k_deg_hist, grid_for(k, 256, p->sm_count * 4), 256, 0, p->A.colptr, ap64, k, hist);
+    s = cuda_check(cudaMemcpyAsync(p->h_pinned + 16, hist, sizeof(int64_t) * 32, cudaMemcpyDeviceToHost, st),
+                   "hub histogram");
+    if (!s) s = cuda_check(cudaStreamSynchronize(st), "hub histogram");
+    if (s) return s;
+    int lg = 0;
+    while ((int64_t(1) << lg) < kHubMinDeg) lg++;
+    int64_t nh = 0;
+    for (; lg < 32; lg++) {
+        nh = 0;
+        for (int b = lg; b < 32; b++) nh += p->h_pinned[16 + b];
+        if ((size_t)nh * (size_t)Wa * sizeof(uint32_t) <= kHubBytes) break;
+    }
+    if (nh == 0 || lg >= 32) return SPG_OK;
+    int32_t *idx = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)k);
+    uint32_t *bits = (uint32_t *)ws_alloc(p, sizeof(uint32_t) * (size_t)(nh * Wa));
+    if (!idx || !bits) return SPG_OUT_OF_MEMORY;
+    s = cuda_check(cudaMemsetAsync(count, 0, sizeof(int), st), "memset");
+    if (!s) s = cuda_check(cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (size_t)(nh * Wa), st), "memset");
+    if (s) return s;
+    launch(p, k_hub_index, grid_for(k, 256, p->sm_count * 4), 256, 0, p->A.colptr, ap64, k, int64_t(1) << lg, idx,
+           count);
+    launch(p, k_hub_bits, grid_for(k * 32, 256, p->sm_count * 8), 256, 0, p->A.colptr, ap64, p->A.rowidx,
+           p->A.idx_type == SPG_IDX_I64, k, p->m, (const int32_t *)idx, Wa, bits);
+    s = cuda_check(cudaGetLastError(), "hub bitmaps");
+    if (s) return s;
+    *hubidx = idx;
+    *hubbits = (uint4 *)bits;
+    *Wa4 = Wa / 4;
+    return SPG_OK;
+}
+
 static spg_status symbolic_heavy(spg_plan *p) {
     spg::PhaseRange nvtx_range("symbolic: heavy columns");
     cudaStream_t st = p->st;
     const int threads = kBatch;
-    size_t smem = sizeof(CtaBatch<long long>) + sizeof(uint32_t) * (size_t)kSymMaxWords;
+    size_t smem = ((sizeof(CtaBatch<long long>) + 15) & ~(size_t)15) + sizeof(uint32_t) * (size_t)kSymMaxWords;
     cudaFuncSetAttribute(k_sym_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sym_heavy, threads, smem);
     if (occ < 1) occ = 1;
     int g = grid_for(p->nsym, 1, p->sm_count * occ);
-    spg_status s0 = cuda_check(cudaMemsetAsync(p->d_cnt + kCntSymNextSlot, 0, sizeof(int64_t), st), "memset");
+    int32_t *hubidx = nullptr;
+    uint4 *hubbits = nullptr;
+    int64_t Wa4 = 0;
+    spg_status s0 = build_hubs(p, &hubidx, &hubbits, &Wa4);
+    if (s0) return s0;
+    s0 = cuda_check(cudaMemsetAsync(p->d_cnt + kCntSymNextSlot, 0, sizeof(int64_t), st), "memset");
     if (s0) return s0;
     group_begin(p, kKSymHeavy);
     launch(p, k_sym_heavy, g, threads, smem, p->nsym, p->sym_rec0, p->sym_nrec, p->rec_col, p->rec_slab,
            p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, p->At_colptr, p->At_row, p->split, p->T, p->R,
            p->hbits, p->rec_cnt, (unsigned long long *)(p->d_cnt + kCntSymNextSlot), p->flops, p->win_lo,
-           p->win_hi, p->omask, (int64_t)((p->m + 31) / 32));
+           p->win_hi, p->omask, (int64_t)((p->m + 31) / 32), (const int32_t *)p->dtilde, (const int32_t *)hubidx,
+           (const uint4 *)hubbits, Wa4, 0);
     group_end(p, kKSymHeavy);
     int64_t *nnum = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
     int64_t *num_first = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(p->nheavy + 1));
