@@ -396,7 +396,7 @@ def main(argv=None):
 
     if not args.no_e2e:
         try:
-            line["e2e"] = run_e2e(g, torch, A, Ai, max(1, min(args.steps, 3)), world, products_step,
+            line["e2e"] = run_e2e(g, torch, A, Ai, max(3, min(args.steps, 8)), world, products_step,
                                   max(st["nnzC"] for sts in stats for st in sts))
         except RuntimeError as ex:   # e.g. no room for C's pinned host pool on this machine (SpgError too)
             line["e2e"] = {"value": None, "unit": "GFLOP/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
@@ -481,6 +481,7 @@ def run_e2e(g, torch, A, Ai, steps, world, products_step, nnzc):
     t_all, flop_all = aggregate(local_s, 2.0 * products_step, world)
     return {"value": flop_all / t_all / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h_total, "steps": len(secs), "ms_per_step": 1e3 * t_all,
+            "ms_per_step_min_max": [round(1e3 * min(secs), 1), round(1e3 * max(secs), 1)],
             "api": f"spgemm_1d_multiply_host (host buffers, {E2E_CHUNKS} groups of column blocks)",
             "timing": "wall clock, synchronize on both sides of each step; every byte of C is in pinned host "
                       f"memory when the call returns (pool of pinned memory allocated once, {pin_s:.1f} s)"}

@@ -326,27 +326,36 @@ def test_similarity_reduced():
 
 
 @pytest.mark.slow
-def test_similarity_full_size_chunk_sampled():
-    """C = A * A^T at full size (A 100,000 x 2^20, lognormal rows, Zipf(1.2)
-    columns, int32 values, int64 result) on the first of the four column chunks
-    the benchmark multiplies, in its launch configuration (P = 4 per chunk,
-    b = 1024, int64 column pointers): sampled columns (the heaviest, random)
-    against the oracle, and the learned-sizing result identical to the exact one."""
+def test_similarity_full_size_every_chunk_sampled():
+    """C = A * A^T at full size on all four column chunks the benchmark
+    multiplies (P = 4 per chunk, b = 1024, int64 column pointers): per chunk
+    the heaviest columns, random ones and both ends against the oracle, the
+    chunk's column counts against the oracle's, and the learned-sizing result
+    identical to the exact one."""
     from paper_2408_14558_gb300 import learned
     A, At = synth.lognormal_zipf_rows(seed=0)
     dA = g.to_device(A, ptr_dtype=torch.int64, idx_dtype=torch.int32)
     dAt = g.to_device(At, ptr_dtype=torch.int64, idx_dtype=torch.int32)
-    c1 = At.ncols // 4
-    s, e = 0, int(dAt.colptr[c1])
-    B = g.DeviceCSC(At.nrows, c1, dAt.colptr[: c1 + 1].contiguous(), dAt.rowidx[s:e], dAt.vals[s:e])
-    C, _ = g.spgemm_1d_multiply(dA, B, P=4, b=1024)
-    fl = oracle.features(A, At, 0, c1)["flops"]
-    rng = np.random.default_rng(1)
-    cols = np.unique(np.concatenate([np.argsort(fl)[-6:], rng.choice(c1, 40, replace=False), [0, c1 - 1]]))
-    assert_sampled_parity(C, A, At, cols, "similarity full-size chunk")
     model = g.spgemm_model_load(learned.DEFAULT_MODEL)
-    Cl, _ = g.spgemm_1d_multiply(dA, B, P=4, b=1024, sizing=g.SPG_SIZING_LEARNED, model=model)
-    torch.cuda.synchronize()
-    assert torch.equal(Cl.colptr, C.colptr)
-    assert torch.equal(Cl.rowidx, C.rowidx)
-    assert torch.equal(Cl.vals, C.vals)
+    n, chunks = At.ncols, 4
+    bounds = [(i * n) // chunks for i in range(chunks + 1)]
+    rng = np.random.default_rng(7)
+    for ch in range(chunks):
+        c0, c1 = bounds[ch], bounds[ch + 1]
+        s, e = int(dAt.colptr[c0]), int(dAt.colptr[c1])
+        B = g.DeviceCSC(At.nrows, c1 - c0, (dAt.colptr[c0:c1 + 1] - s).contiguous(), dAt.rowidx[s:e],
+                        dAt.vals[s:e])
+        C, _ = g.spgemm_1d_multiply(dA, B, P=4, b=1024)
+        f = oracle.features(A, At, c0, c1)
+        cols = np.unique(np.concatenate([np.argsort(f["flops"])[-4:], rng.choice(c1 - c0, 24, replace=False),
+                                         [0, c1 - c0 - 1]]))
+        Bh = synth.CSC(At.nrows, c1 - c0, np.asarray(At.colptr[c0:c1 + 1], dtype=np.int64) - s,
+                       np.asarray(At.rowidx[s:e]), np.asarray(At.vals[s:e]))
+        assert_sampled_parity(C, A, Bh, cols, f"similarity chunk {ch}")
+        Cl, _ = g.spgemm_1d_multiply(dA, B, P=4, b=1024, sizing=g.SPG_SIZING_LEARNED, model=model)
+        torch.cuda.synchronize()
+        assert torch.equal(Cl.colptr, C.colptr), ch
+        assert torch.equal(Cl.rowidx, C.rowidx), ch
+        assert torch.equal(Cl.vals, C.vals), ch
+        del C, Cl, B
+        torch.cuda.empty_cache()
