@@ -8,15 +8,12 @@ namespace spg {
 
 // Staging area of cta_products for one batch of kBatch B' entries: the
 // non-empty A~ segments they multiply.  Long segments (>= kLongSeg entries)
-// sit at [0, nl) and are walked in chunks of 32 entries, one chunk per warp
-// step; short ones sit at [nl, nl + ns) and are packed one product per lane.
-// pref holds the exclusive prefix of the chunk counts (long part) and of the
-// product counts (short part).
+// sit at [0, nl), short ones at [nl, nl + ns); each part numbers its products
+// consecutively and pref holds a segment's first product in that numbering.
 template <typename Acc>
 struct CtaBatch {
     long long start[kBatch];
     int pref[kBatch + 2];
-    int len[kBatch];
     Acc bv[kBatch];
     int wsum[4][33];
 };
@@ -73,13 +70,15 @@ __device__ __forceinline__ SegReg<Acc> cta_first_seg(int64_t p0, int64_t p1, Seg
 // seg(p, start, len, bv) gives the A~ positions [start, start+len) that B'
 // entry p multiplies and its value; body(row, product) runs once per product.
 // The segments of the next batch are fetched before the current batch is
-// walked.  The chunks of the long segments are shared evenly by the warps
-// (lanes read consecutive entries, coalesced); each warp step takes the next U
-// chunks of the warp's range, across segment boundaries, so that U loads per
-// lane are in flight however short the segments.  The products of short
-// segments are shared evenly too (a warp bitmask locates each lane's
+// walked.  The products of the long segments are shared evenly by the warps
+// (lanes read consecutive entries, coalesced); each warp step takes the next
+// 32 x U products of the warp's range, across segment boundaries, so that U
+// loads per lane are in flight however the segments fall.  The products of
+// short segments are shared evenly too (a warp bitmask locates each lane's
 // segment).  One batch must hold < 2^31 products (heavy items bound their
 // segments to the item's row range).  Ends with a barrier.
+static_assert(kLongSeg >= 32, "a 32-product window must meet at most two long segments");
+
 template <bool NEED_VAL, int U, typename Acc, typename SegFn, typename Body>
 __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Acc> &sb,
                                              const int32_t *__restrict__ At_row, const Acc *__restrict__ At_val,
@@ -91,15 +90,13 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
         const int len = cur.len;
         const Acc bv = cur.bv;
         const bool is_long = len >= kLongSeg;
-        const int v[4] = {is_long ? 1 : 0, is_long ? (len + 31) >> 5 : 0, (!is_long && len > 0) ? 1 : 0,
-                          is_long ? 0 : len};
+        const int v[4] = {is_long ? 1 : 0, is_long ? len : 0, (!is_long && len > 0) ? 1 : 0, is_long ? 0 : len};
         int ex[4], tot[4];
         cta_scan4(v, ex, sb.wsum, tot);
-        const int nl = tot[0], nch = tot[1], ns = tot[2], nsp = tot[3];
+        const int nl = tot[0], nlp = tot[1], ns = tot[2], nsp = tot[3];
         if (is_long) {
             sb.start[ex[0]] = st;
             sb.pref[ex[0]] = ex[1];
-            sb.len[ex[0]] = len;
             if (NEED_VAL) sb.bv[ex[0]] = bv;
         } else if (len > 0) {
             sb.start[nl + ex[2]] = st;
@@ -109,55 +106,56 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
         __syncthreads();
         if (b0 + kBatch < p1) cur = cta_first_seg<Acc>(b0 + kBatch, p1, seg);
 
-        // long segments: chunks [c0, c1) of this warp, U per step
+        // long segments: products [f0, f1) of this warp in the long
+        // segments' own numbering (no padding between segments), 32 per warp
+        // step, U steps in flight.  A long segment holds >= 32 products, so a
+        // window of 32 consecutive products meets at most two segments (the
+        // current one, A, and the next, B) and crosses at most one boundary
+        // per step.  Each segment's start is kept minus its product prefix,
+        // so product f of it is entry base + f of A~.
         {
-            const int per = (nch + nw - 1) / nw;
-            const int c0 = wid * per, c1 = min(nch, c0 + per);
-            if (c0 < c1) {
+            const int per = (nlp + nw - 1) / nw;
+            const int f0 = wid * per, f1 = min(nlp, f0 + per);
+            if (f0 < f1) {
                 int s = 0;
                 for (int stp = kBatch >> 1; stp > 0; stp >>= 1)
-                    if (s + stp < nl && sb.pref[s + stp] <= c0) s += stp;
-                // segment s (chunks [sp, snext)) in registers; chunks are
-                // contiguous and every long segment has one or more, so the
-                // next chunk lies in s or s + 1
-                int sp = sb.pref[s], slen = sb.len[s];
-                int snext = s + 1 < nl ? sb.pref[s + 1] : nch;
-                const int32_t *srp = At_row + sb.start[s];
-                const Acc *svp = NEED_VAL ? At_val + sb.start[s] : nullptr;
-                Acc sbv = NEED_VAL ? sb.bv[s] : Acc(0);
-                for (int c = c0; c < c1; c += U) {
+                    if (s + stp < nl && sb.pref[s + stp] <= f0) s += stp;
+                long long baseA = sb.start[s] - sb.pref[s];
+                Acc bvA = NEED_VAL ? sb.bv[s] : Acc(0);
+                int nB = s + 1 < nl ? sb.pref[s + 1] : nlp;  // first product of B
+                long long baseB = 0;
+                Acc bvB = Acc(0);
+                if (s + 1 < nl) {
+                    baseB = sb.start[s + 1] - nB;
+                    if (NEED_VAL) bvB = sb.bv[s + 1];
+                }
+                for (int f = f0; f < f1; f += 32 * U) {
                     int r[U];
                     Acc a[U], bu[U];
                     bool ok[U];
 #pragma unroll
                     for (int u = 0; u < U; u++) {
-                        const int cu = c + u;
-                        ok[u] = false;
+                        const int fb = f + 32 * u;
+                        if (fb >= nB) {  // the window starts in B: B becomes A
+                            s++;
+                            baseA = baseB;
+                            bvA = bvB;
+                            nB = s + 1 < nl ? sb.pref[s + 1] : nlp;
+                            if (s + 1 < nl) {
+                                baseB = sb.start[s + 1] - nB;
+                                if (NEED_VAL) bvB = sb.bv[s + 1];
+                            }
+                        }
+                        const int fi = fb + lane;
+                        const bool inB = fi >= nB;
+                        const long long e = (inB ? baseB : baseA) + fi;
+                        ok[u] = fi < f1;
                         r[u] = 0;
                         a[u] = Acc(0);
-                        bu[u] = Acc(0);
-                        if (cu < c1) {
-                            if (cu == snext) {
-                                s++;
-                                sp = snext;
-                                slen = sb.len[s];
-                                const long long st2 = sb.start[s];
-                                srp = At_row + st2;
-                                if (NEED_VAL) {
-                                    svp = At_val + st2;
-                                    sbv = sb.bv[s];
-                                }
-                                snext = s + 1 < nl ? sb.pref[s + 1] : nch;
-                            }
-                            const int off = ((cu - sp) << 5) + lane;
-                            if (off < slen) {
-                                ok[u] = true;
-                                r[u] = __ldg(srp + off);
-                                if (NEED_VAL) {
-                                    a[u] = __ldg(svp + off);
-                                    bu[u] = sbv;
-                                }
-                            }
+                        bu[u] = inB ? bvB : bvA;
+                        if (ok[u]) {
+                            r[u] = __ldg(At_row + e);
+                            if (NEED_VAL) a[u] = __ldg(At_val + e);
                         }
                     }
 #pragma unroll
