@@ -71,7 +71,8 @@ constexpr int kHeavyCap = 4096;        // entries of one numeric window
 constexpr int kBatchMaxLogS = 11;  // per-warp tables of up to 2048 slots
 // Instances are launched in three classes by the table their largest column
 // needs (up to 512, 1024 and 2048 slots), each class by its own persistent
-// kernel, so that small tables buy more resident warps.
+// kernel, so that small tables buy more resident warps; the three kernels are
+// parallel branches of the graph.
 constexpr int kBatchClasses = 3;
 constexpr int kBatchClassLogS[kBatchClasses] = {9, 10, 11};
 enum : int { kBatchErrTimeout = 8 };
@@ -212,7 +213,8 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
                 if (heavy_col[colb + j]) continue;  // counted by the heavy kernel
                 const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
                 // the class's largest table: every column's bound min(flops, m)
-                // is <= S_MAX / 2, so it needs no pass of its own
+                // is <= S_MAX / 2, so it needs no pass of its own (a table
+                // sized from the column's own bound probes more: slower)
                 const int logS = LOGS_MAX;
                 const int S = 1 << logS;
                 for (int s = lane; s < S; s += 32) keys[s] = kEmptyKey;
@@ -250,7 +252,9 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
                 const int64_t base = in.out_base + cp[j];
                 const int64_t want = cp[j + 1] - cp[j];
                 const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
-                const int logS = log_table(want > 0 ? want : 1);
+                // >= 4 x the column's count (at most the class's table): a
+                // sparser table probes less, which outweighs clearing more
+                const int logS = min(LOGS_MAX, log_table(want > 0 ? want : 1) + 1);
                 const int S = 1 << logS;
                 for (int s = lane; s < S; s += 32) {
                     keys[s] = kEmptyKey;
@@ -438,6 +442,8 @@ struct spg_batch {
     bool f64 = true;
     spg_batch_options opt{};
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side[spg::kBatchClasses] = {};  // branches of the captured graph (class c > 0)
+    cudaEvent_t fork = nullptr, join[spg::kBatchClasses] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<spg::BatchInst> hinst;
@@ -487,6 +493,11 @@ extern "C" spg_status spgemm_batch_destroy(spg_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int c = 0; c < kBatchClasses; c++) {
+        if (b->side[c]) cudaStreamDestroy(b->side[c]);
+        if (b->join[c]) cudaEventDestroy(b->join[c]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     cudaDeviceSynchronize();
     for (void *p : b->allocs) cudaFree(p);
     delete b;
@@ -494,7 +505,7 @@ extern "C" spg_status spgemm_batch_destroy(spg_batch *b) {
 }
 
 template <int LOGS_MAX, typename Acc, typename OutIdx>
-static spg_status batch_launch_class(spg_batch *b, int c) {
+static spg_status batch_launch_class(spg_batch *b, int c, cudaStream_t st) {
     const int64_t t0 = b->class_off[c], nt = b->class_off[c + 1] - t0;
     if (nt == 0) return SPG_OK;
     auto kern = k_batch_persistent<LOGS_MAX, Acc, OutIdx>;
@@ -512,7 +523,7 @@ static spg_status batch_launch_class(spg_batch *b, int c) {
     const int grid = b->sm_count * occ;
     b->grid = std::max(b->grid, grid);
     b->smem = std::max(b->smem, smem);
-    kern<<<grid, b->warps * 32, smem, b->cap_stream>>>(
+    kern<<<grid, b->warps * 32, smem, st>>>(
         b->insts, b->tasks + t0, nt, b->head + c, b->sym_done, b->ready, b->nnz, b->colptr, (OutIdx *)b->out_row,
         (Acc *)b->out_val, b->err, b->opt.timeout_ns, b->opt.stall_instance, b->heavy_col);
     return cuda_check(cudaGetLastError(), "batch kernel launch");
@@ -541,7 +552,8 @@ static spg_status batch_launch_heavy(spg_batch *b) {
     return cuda_check(cudaGetLastError(), "batch heavy kernel launch");
 }
 
-// One graph: clear the counters and flags, then the class kernels in turn.
+// One graph: clear the counters and flags, the heavy columns' counts, the
+// three class kernels side by side, then the heavy columns' values.
 template <typename Acc, typename OutIdx>
 static spg_status batch_capture(spg_batch *b) {
     spg_status s = cuda_check(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
@@ -553,9 +565,20 @@ static spg_status batch_capture(spg_batch *b) {
     // then scans counts that are all there; heavy values last: their
     // instances' column pointers are published by then
     s = batch_launch_heavy<0, Acc, OutIdx>(b);
-    if (!s) s = batch_launch_class<kBatchClassLogS[0], Acc, OutIdx>(b, 0);
-    if (!s) s = batch_launch_class<kBatchClassLogS[1], Acc, OutIdx>(b, 1);
-    if (!s) s = batch_launch_class<kBatchClassLogS[2], Acc, OutIdx>(b, 2);
+    // the class kernels as parallel branches of the graph: a class's CTAs take
+    // the SMs that another class's CTAs leave as its queue drains (each
+    // kernel's waits are on its own warps' tasks only)
+    cudaStream_t cst[kBatchClasses] = {b->cap_stream, b->side[1], b->side[2]};
+    if (!s) s = cuda_check(cudaEventRecord(b->fork, b->cap_stream), "fork");
+    for (int c = 1; c < kBatchClasses && !s; c++) s = cuda_check(cudaStreamWaitEvent(cst[c], b->fork, 0), "fork");
+    if (!s) s = batch_launch_class<kBatchClassLogS[0], Acc, OutIdx>(b, 0, cst[0]);
+    if (!s) s = batch_launch_class<kBatchClassLogS[1], Acc, OutIdx>(b, 1, cst[1]);
+    if (!s) s = batch_launch_class<kBatchClassLogS[2], Acc, OutIdx>(b, 2, cst[2]);
+    for (int c = 1; c < kBatchClasses; c++) {
+        // joined even after an error, so that the capture can end
+        cudaEventRecord(b->join[c], cst[c]);
+        cudaStreamWaitEvent(b->cap_stream, b->join[c], 0);
+    }
     if (!s) s = batch_launch_heavy<1, Acc, OutIdx>(b);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
@@ -601,6 +624,11 @@ extern "C" spg_status spgemm_batch_create(int32_t count, const spg_csc *A, const
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
     spg_status s = cuda_check(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream");
+    for (int c = 1; c < kBatchClasses && !s; c++) {
+        s = cuda_check(cudaStreamCreateWithFlags(&b->side[c], cudaStreamNonBlocking), "stream");
+        if (!s) s = cuda_check(cudaEventCreateWithFlags(&b->join[c], cudaEventDisableTiming), "event");
+    }
+    if (!s) s = cuda_check(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
     // instances and tasks
     std::vector<BatchTask> htask;
     b->hinst.resize(count);
