@@ -321,7 +321,12 @@ spg_status spgemm_autotune(const spg_csc *A, const spg_csc *B, const spg_options
  * spgemm_1d_multiply sizes every column's output room from the prediction
  * (times learned_slack, at most the exact bound min(flops_j, row window)),
  * runs the numeric work without the symbolic pass and recomputes the columns
- * that overflow through the exact path; C is the exact path's C.
+ * that overflow through the exact path; C is the exact path's C.  The heavy
+ * columns run in groups; each finished group is placed in C while the next
+ * one computes, so C's row and value arrays are allocated at the predicted
+ * capacity (spg_stats.learned_capacity entries, of which the first nnz(C)
+ * hold C).  When a column overflows, C is instead assembled after the
+ * recompute, at its exact size.  Learned sizing needs slab_rows <= 4096.
  * Parameters: one flat float vector of SPG_MODEL_NPARAMS entries, laid out
  * W1 (32 x 4, row-major by hidden unit) | b1 (32) | W2 (32 x 32) | b2 (32) |
  * w3 (32) | b3 (1).  X arrays are n x 4 row-major device floats; y, out are

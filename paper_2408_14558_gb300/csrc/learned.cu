@@ -13,8 +13,11 @@
 //          warp-shuffle reduction of every gradient component), k_adam.
 //   learned multiply: light columns use warp hash tables sized from the
 //          prediction; heavy columns use a fused one-pass kernel (dense row
-//          accumulator + row bitmap per 8192-row item) whose counts are exact;
-//          then the overflowed columns are recomputed and C is assembled.
+//          accumulator + row bitmap per 4096-row item) whose counts are exact,
+//          in groups of heavy columns, each group placed in C (on a second
+//          stream) while the next one computes; overflowed columns are
+//          recomputed and C is then assembled after them.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -33,7 +36,7 @@ constexpr int kW1 = 0, kB1 = kW1 + kH * kF, kW2 = kB1 + kH, kB2 = kW2 + kH * kH,
 constexpr int kNP = kB3 + 1;  // 1249
 static_assert(kNP == 1249, "parameter layout");
 #ifndef SPG_FUSED_ROWS
-#define SPG_FUSED_ROWS 8192
+#define SPG_FUSED_ROWS 4096
 #endif
 constexpr int kFusedRows = SPG_FUSED_ROWS;  // rows of one fused heavy item (dense accumulator in shared memory)
 
@@ -308,7 +311,8 @@ __global__ void __launch_bounds__(WARPS * 32)
 // order, one bitmap word per warp step (the set bits of a word are consecutive
 // entries: coalesced).  An item that does not fit flags its column (the count
 // still adds to colfill, which ends as the exact nnz).  The accumulator is
-// cleared as it is read, so it is zero again for the next item.
+// cleared as it is read, so it is zero again for the next item.  One launch
+// takes the items [it_begin, it_begin + nitems).
 template <typename Acc, typename OutIdx>
 __global__ void __launch_bounds__(kBatch)
     k_fused_heavy(int64_t nitems, const int32_t *__restrict__ it_rec0, const int32_t *__restrict__ it_nrec,
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(kBatch)
                   const int64_t *__restrict__ capoff, const int64_t *__restrict__ cap,
                   unsigned long long *__restrict__ colfill, int32_t *flag, unsigned long long *nflag,
                   int32_t *__restrict__ item_cnt, int64_t *__restrict__ item_pos, OutIdx *__restrict__ trow,
-                  Acc *__restrict__ tval, unsigned long long *next) {
+                  Acc *__restrict__ tval, unsigned long long *next, int64_t it_begin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaBatch<Acc> &sb = *(CtaBatch<Acc> *)smem_raw;
     unsigned char *acc_raw = smem_raw + ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15);
@@ -331,7 +335,8 @@ __global__ void __launch_bounds__(kBatch)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = threadIdx.x; i < kFusedRows; i += blockDim.x) acc.zero(i);
     const int RW = R >> 5;
-    for (int64_t it = cta_claim(next, &claim); it < nitems; it = cta_claim(next, &claim)) {
+    for (int64_t li = cta_claim(next, &claim); li < nitems; li = cta_claim(next, &claim)) {
+        const int64_t it = it_begin + li;
         const int r0 = it_rec0[it], nr = it_nrec[it];
         const int j = rec_col[r0], t0 = rec_slab[r0];
         const int nwords = nr * RW;
@@ -414,6 +419,58 @@ __global__ void k_learned_nnz(int64_t n, const int8_t *bin_of, const unsigned lo
     if ((threadIdx.x & 31) == 0 && hsum) atomicAdd(heavy_sum, hsum);
 }
 
+// The same for the columns [c0, c1) of one group of the pipelined assembly;
+// a flagged column (its count is not known yet) marks the order broken:
+// later columns cannot be placed before the recompute.
+__global__ void k_learned_nnz_range(int64_t c0, int64_t c1, const int8_t *bin_of,
+                                    const unsigned long long *colfill, const int64_t *nnz_light,
+                                    const int32_t *flag, int64_t *nnz, unsigned long long *heavy_sum,
+                                    int *broken) {
+    unsigned long long hsum = 0;
+    bool any = false;
+    for (int64_t j = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < c1;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int b = bin_of[j];
+        int64_t v = 0;
+        if (flag[j]) {
+            any = true;
+        } else if (b == kBinHeavy) {
+            v = (int64_t)colfill[j];
+            hsum += (unsigned long long)v;
+        } else if (b != kBinEmpty) {
+            v = nnz_light[j];
+        }
+        nnz[j] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, o);
+    if ((threadIdx.x & 31) == 0 && hsum) atomicAdd(heavy_sum, hsum);
+    if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(broken, 1);
+}
+
+// Canonical column pointers of one group: the group's exclusive scan
+// local[0..len] plus the entries of all earlier groups (carry[g]); the
+// group's end goes to carry[g + 1].
+__global__ void k_add_carry(const int64_t *local, int64_t len, const int64_t *carry_in, int64_t *carry_out,
+                            int64_t *colptr) {
+    const int64_t c = *carry_in;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= len; i += (int64_t)gridDim.x * blockDim.x)
+        colptr[i] = c + local[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *carry_out = c + local[len];
+}
+
+// Boundaries of the pipelined assembly's groups: for g = 0..G, the first item
+// of heavy column hb[g] and the first column of group g (0 for the first
+// group, n past the last one, else the id of the group's first heavy column;
+// the heavy list is in column order).
+__global__ void k_group_bounds(const int64_t *hb, int64_t G, int64_t nheavy, const int32_t *heavy_list,
+                               const int64_t *it_first, int64_t n, int64_t *out) {
+    for (int64_t g = threadIdx.x; g <= G; g += blockDim.x) {
+        const int64_t h = hb[g];
+        out[2 * g] = it_first[h];
+        out[2 * g + 1] = g == 0 ? 0 : (g == G || h >= nheavy ? n : (int64_t)heavy_list[h]);
+    }
+}
+
 // Position of every flagged column in the list of flagged columns.
 __global__ void k_flag_list(int64_t n, const int32_t *flag, const int64_t *fpos, int32_t *list) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
@@ -456,8 +513,9 @@ __global__ void k_put_flagged_nnz(int64_t nf, const int32_t *list, const int64_t
 
 // Canonical offset of every fused item inside its column: items of a column
 // are generated in row order, so the offset is the sum of earlier counts.
-__global__ void k_item_canon(int64_t nheavy, const int64_t *it_first, const int32_t *item_cnt, int64_t *canon) {
-    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nheavy; h += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_item_canon(int64_t h0, int64_t h1, const int64_t *it_first, const int32_t *item_cnt,
+                             int64_t *canon) {
+    for (int64_t h = h0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < h1; h += (int64_t)gridDim.x * blockDim.x) {
         int64_t off = 0;
         for (int64_t it = it_first[h]; it < it_first[h + 1]; it++) {
             canon[it] = off;
@@ -466,14 +524,17 @@ __global__ void k_item_canon(int64_t nheavy, const int64_t *it_first, const int3
     }
 }
 
+// Light columns [c0, c1) from the predicted layout to C (nothing when
+// `broken` is set: their places in C are not known).
 template <typename Acc, typename OutIdx>
-__global__ void k_copy_light(int64_t n, const int8_t *bin_of, const int32_t *flag, const int64_t *capoff,
-                             const int64_t *nnz, const int64_t *Ccolptr, const OutIdx *trow, const Acc *tval,
-                             OutIdx *Crow, Acc *Cval) {
+__global__ void k_copy_light(int64_t c0, int64_t c1, const int8_t *bin_of, const int32_t *flag,
+                             const int64_t *capoff, const int64_t *nnz, const int64_t *Ccolptr, const OutIdx *trow,
+                             const Acc *tval, OutIdx *Crow, Acc *Cval, const int *broken) {
+    if (broken && *(volatile const int *)broken) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = warp; j < n; j += nw) {
+    for (int64_t j = c0 + warp; j < c1; j += nw) {
         const int b = bin_of[j];
         if (b == kBinHeavy || b == kBinEmpty || flag[j]) continue;
         const int64_t s = capoff[j], d = Ccolptr[j], len = nnz[j];
@@ -484,12 +545,15 @@ __global__ void k_copy_light(int64_t n, const int8_t *bin_of, const int32_t *fla
     }
 }
 
+// Fused items [i0, i1) from the predicted layout to C (nothing when `broken`
+// is set).
 template <typename Acc, typename OutIdx>
-__global__ void k_copy_items(int64_t nitems, const int32_t *it_rec0, const int32_t *rec_col, const int32_t *flag,
-                             const int64_t *capoff, const int32_t *item_cnt, const int64_t *item_pos,
-                             const int64_t *canon, const int64_t *Ccolptr, const OutIdx *trow, const Acc *tval,
-                             OutIdx *Crow, Acc *Cval) {
-    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+__global__ void k_copy_items(int64_t i0, int64_t i1, const int32_t *it_rec0, const int32_t *rec_col,
+                             const int32_t *flag, const int64_t *capoff, const int32_t *item_cnt,
+                             const int64_t *item_pos, const int64_t *canon, const int64_t *Ccolptr,
+                             const OutIdx *trow, const Acc *tval, OutIdx *Crow, Acc *Cval, const int *broken) {
+    if (broken && *(volatile const int *)broken) return;
+    for (int64_t it = i0 + blockIdx.x; it < i1; it += gridDim.x) {
         const int j = rec_col[it_rec0[it]];
         if (flag[j]) continue;
         const int64_t s = capoff[j] + item_pos[it], d = Ccolptr[j] + canon[it];
@@ -791,6 +855,11 @@ static spg_status launch_light_learned(spg_plan *p, const int32_t *list, int64_t
     return cuda_check(cudaGetLastError(), "learned light");
 }
 
+// Groups of heavy columns in the pipelined assembly (pinned read-back slots
+// 24 .. 24 + 2 * (groups + 1) of the plan hold their boundaries).
+constexpr int64_t kLearnedGroups = 8;
+static_assert(24 + 2 * (kLearnedGroups + 1) <= 63, "pinned slots");
+
 struct LearnedState {
     int64_t *cap = nullptr, *capoff = nullptr, *nnz_light = nullptr, *nnz = nullptr;
     int8_t *lbin = nullptr;
@@ -805,10 +874,9 @@ struct LearnedState {
 };
 
 template <typename Acc, typename OutIdx>
-static spg_status learned_kernels(spg_plan *p, LearnedState &L) {
+static spg_status learned_light(spg_plan *p, LearnedState &L) {
     spg_status s = SPG_OK;
-    // light columns and the fused heavy pass are timed as the light and heavy
-    // numeric groups
+    // timed as the light numeric group
     group_begin(p, kKNumLight);
     for (int bin = 1; bin <= kMaxLightBin && !s; bin++) {
         int64_t cnt = L.loff[bin + 1] - L.loff[bin];
@@ -824,7 +892,14 @@ static spg_status learned_kernels(spg_plan *p, LearnedState &L) {
         }
     }
     group_end(p, kKNumLight);
-    if (s || L.nitems == 0) return s;
+    return s;
+}
+
+// The fused heavy pass over items [i0, i1) (one persistent launch on the
+// plan's stream, its own item counter).
+template <typename Acc, typename OutIdx>
+static spg_status learned_fused(spg_plan *p, LearnedState &L, int64_t i0, int64_t i1) {
+    if (i1 <= i0) return SPG_OK;
     size_t smem = ((sizeof(CtaBatch<Acc>) + 15) & ~(size_t)15) + sizeof(Acc) * kFusedRows +
                   sizeof(uint32_t) * (kFusedRows / 32) + sizeof(int) * (kFusedRows / 32 + 1);
     auto kern = k_fused_heavy<Acc, OutIdx>;
@@ -834,27 +909,79 @@ static spg_status learned_kernels(spg_plan *p, LearnedState &L) {
     int occ = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBatch, smem);
     if (occ < 1) occ = 1;
-    group_begin(p, kKNumHeavy);
-    launch(p, kern, grid_for(L.nitems, 1, p->sm_count * occ), kBatch, smem, L.nitems, L.it_rec0, L.it_nrec, p->rec_col,
+    launch(p, kern, grid_for(i1 - i0, 1, p->sm_count * occ), kBatch, smem, i1 - i0, L.it_rec0, L.it_nrec, p->rec_col,
            p->rec_slab, p->B.colptr, p->B.ptr_type == SPG_IDX_I64, p->Bq, (const Acc *)p->Bv, p->At_colptr, p->At_row,
            (const Acc *)p->At_val, p->split, p->T, p->R, L.capoff, L.cap, L.colfill, L.flag, L.nflag, L.item_cnt,
-           L.item_pos, (OutIdx *)L.trow, (Acc *)L.tval, (unsigned long long *)(p->d_cnt + kCntFusedNextSlot));
-    group_end(p, kKNumHeavy);
+           L.item_pos, (OutIdx *)L.trow, (Acc *)L.tval, (unsigned long long *)(p->d_cnt + kCntFusedNextSlot), i0);
     return cuda_check(cudaGetLastError(), "fused heavy");
+}
+
+// Launch on a given stream (counted with the plan's launches).
+template <typename... KArgs, typename... Args>
+static void launch_on(spg_plan *p, cudaStream_t st, void (*kern)(KArgs...), dim3 grid, dim3 block, Args &&...args) {
+    p->launches++;
+    kern<<<grid, block, 0, st>>>(static_cast<KArgs>(args)...);
+}
+
+// Pipelined assembly, group g of G: once the fused items of heavy columns
+// [h0, h1) are done (event `done` on the plan's stream), the side stream
+// counts the columns [c0, c1), places them after all earlier groups and
+// copies their light columns and items into C, while the plan's stream goes
+// on with the next group's items.
+template <typename Acc, typename OutIdx>
+static spg_status learned_place_group(spg_plan *p, LearnedState &L, cudaStream_t side, int g, int64_t c0, int64_t c1,
+                                      int64_t h0, int64_t h1, int64_t i0, int64_t i1, int64_t *local, int64_t *carry,
+                                      int *broken, spg_csc *C) {
+    const int sm = p->sm_count;
+    const int64_t len = c1 - c0;
+    if (len > 0) {
+        launch_on(p, side, k_learned_nnz_range, grid_for(len, 256, sm * 8), 256, c0, c1, (const int8_t *)p->bin_of,
+                  (const unsigned long long *)L.colfill, (const int64_t *)L.nnz_light, (const int32_t *)L.flag, L.nnz,
+                  (unsigned long long *)(p->d_cnt + kCntNnzCHeavySlot), broken);
+        // the group's scan runs on the side stream too
+        cudaStream_t keep = p->st;
+        p->st = side;
+        spg_status s = scan_exclusive_i64(p, L.nnz + c0, local, len);
+        p->st = keep;
+        if (s) return s;
+    } else {
+        cuda_check(cudaMemsetAsync(local, 0, sizeof(int64_t), side), "memset");
+    }
+    launch_on(p, side, k_add_carry, grid_for(len + 1, 256, sm * 8), 256, (const int64_t *)local, len,
+              (const int64_t *)(carry + g), carry + g + 1, p->Ccolptr + c0);
+    if (len > 0)
+        launch_on(p, side, k_copy_light<Acc, OutIdx>, grid_for(len * 32, 256, sm * 4), 256, c0, c1,
+                  (const int8_t *)p->bin_of, (const int32_t *)L.flag, (const int64_t *)L.capoff,
+                  (const int64_t *)L.nnz, (const int64_t *)p->Ccolptr, (const OutIdx *)L.trow, (const Acc *)L.tval,
+                  (OutIdx *)C->rowidx, (Acc *)C->vals, (const int *)broken);
+    if (h1 > h0) {
+        launch_on(p, side, k_item_canon, grid_for(h1 - h0, 256, sm * 8), 256, h0, h1, (const int64_t *)L.it_first,
+                  (const int32_t *)L.item_cnt, L.canon);
+        launch_on(p, side, k_copy_items<Acc, OutIdx>, grid_for(i1 - i0, 1, sm * 4), 256, i0, i1,
+                  (const int32_t *)L.it_rec0, (const int32_t *)p->rec_col, (const int32_t *)L.flag,
+                  (const int64_t *)L.capoff, (const int32_t *)L.item_cnt, (const int64_t *)L.item_pos,
+                  (const int64_t *)L.canon, (const int64_t *)p->Ccolptr, (const OutIdx *)L.trow, (const Acc *)L.tval,
+                  (OutIdx *)C->rowidx, (Acc *)C->vals, (const int *)broken);
+    }
+    return cuda_check(cudaGetLastError(), "learned group");
 }
 
 template <typename Acc, typename OutIdx>
 static spg_status learned_assemble(spg_plan *p, LearnedState &L, int64_t nf, const int32_t *flist,
                                    const int64_t *fcolptr, const void *frow, const void *fval, spg_csc *C) {
     const int sm = p->sm_count;
-    launch(p, k_copy_light<Acc, OutIdx>, grid_for(p->n * 32, 256, sm * 16), 256, 0, p->n, p->bin_of, L.flag,
-           L.capoff, L.nnz, p->Ccolptr, (const OutIdx *)L.trow, (const Acc *)L.tval, (OutIdx *)C->rowidx,
-           (Acc *)C->vals);
+    launch(p, k_copy_light<Acc, OutIdx>, grid_for(p->n * 32, 256, sm * 16), 256, 0, (int64_t)0, p->n,
+           (const int8_t *)p->bin_of, (const int32_t *)L.flag, (const int64_t *)L.capoff, (const int64_t *)L.nnz,
+           (const int64_t *)p->Ccolptr, (const OutIdx *)L.trow, (const Acc *)L.tval, (OutIdx *)C->rowidx,
+           (Acc *)C->vals, (const int *)nullptr);
     if (L.nitems > 0) {
-        launch(p, k_item_canon, grid_for(p->nheavy, 256, sm * 8), 256, 0, p->nheavy, L.it_first, L.item_cnt, L.canon);
-        launch(p, k_copy_items<Acc, OutIdx>, grid_for(L.nitems, 1, sm * 8), 256, 0, L.nitems, L.it_rec0, p->rec_col,
-               L.flag, L.capoff, L.item_cnt, L.item_pos, L.canon, p->Ccolptr, (const OutIdx *)L.trow,
-               (const Acc *)L.tval, (OutIdx *)C->rowidx, (Acc *)C->vals);
+        launch(p, k_item_canon, grid_for(p->nheavy, 256, sm * 8), 256, 0, (int64_t)0, p->nheavy,
+               (const int64_t *)L.it_first, (const int32_t *)L.item_cnt, L.canon);
+        launch(p, k_copy_items<Acc, OutIdx>, grid_for(L.nitems, 1, sm * 8), 256, 0, (int64_t)0, L.nitems,
+               (const int32_t *)L.it_rec0, (const int32_t *)p->rec_col, (const int32_t *)L.flag,
+               (const int64_t *)L.capoff, (const int32_t *)L.item_cnt, (const int64_t *)L.item_pos,
+               (const int64_t *)L.canon, (const int64_t *)p->Ccolptr, (const OutIdx *)L.trow, (const Acc *)L.tval,
+               (OutIdx *)C->rowidx, (Acc *)C->vals, (const int *)nullptr);
     }
     if (nf > 0)
         launch(p, k_copy_flagged<Acc, OutIdx>, grid_for(nf * 32, 256, sm * 16), 256, 0, nf, flist, fcolptr,
@@ -956,22 +1083,151 @@ static spg_status learned_run(spg_plan *p, const spg_options *opt, spg_csc *C, i
                (const int64_t *)L.it_first, L.it_rec0, L.it_nrec);
     }
 
-    // 3. the learned numeric work
-    spg_status s;
-    if (p->acc_f64)
-        s = p->out_idx64 ? learned_kernels<double, long long>(p, L) : learned_kernels<double, int>(p, L);
-    else
-        s = p->out_idx64 ? learned_kernels<long long, long long>(p, L) : learned_kernels<long long, int>(p, L);
-    if (s) return s;
+    // 3. the learned numeric work: light columns, then the fused items in G
+    // groups of heavy columns; as soon as a group's items are done, a side
+    // stream counts its columns, places them after the earlier groups and
+    // copies them into C (allocated at the predicted capacity) while the next
+    // group computes.  A column that overflowed its room stops the placement
+    // (its count is known only after the recompute): C is then assembled
+    // after the recompute instead, from the predicted layout.
+    const size_t cp_bytes = sizeof(int64_t) * (size_t)(n + 1);
+    const size_t ri_bytes = idxsz * (size_t)(totcap + 1), va_bytes = 8 * (size_t)(totcap + 1);
+    void *cp_opt = alloc_out(opt, cp_bytes);
+    void *ri_opt = alloc_out(opt, ri_bytes);
+    void *va_opt = alloc_out(opt, va_bytes);
+    auto free_opt = [&]() {
+        free_out(opt, cp_opt, cp_bytes);
+        free_out(opt, ri_opt, ri_bytes);
+        free_out(opt, va_opt, va_bytes);
+        cp_opt = ri_opt = va_opt = nullptr;
+    };
+    if (!cp_opt || !ri_opt || !va_opt) {
+        free_opt();
+        set_error("allocation of C at the predicted capacity (%lld entries) failed", (long long)totcap);
+        return SPG_OUT_OF_MEMORY;
+    }
+    spg_csc Copt{};
+    Copt.rowidx = ri_opt;
+    Copt.vals = va_opt;
+    const int64_t G = p->nrec > 0 ? std::min<int64_t>(kLearnedGroups, p->nheavy) : 0;
+    // group boundaries: heavy columns hb[g], items ib[g], columns cb[g]
+    std::vector<int64_t> hb(G + 1), ib(G + 1, 0), cb(G + 2, 0);
+    int64_t *carry = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(G + 2));
+    int64_t *local = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(n + 2));
+    int *broken = (int *)ws_alloc(p, sizeof(int));
+    int64_t *bnd = (int64_t *)ws_alloc(p, sizeof(int64_t) * 2 * (size_t)(G + 1));
+    if (!carry || !local || !broken || !bnd) {
+        free_opt();
+        return SPG_OUT_OF_MEMORY;
+    }
+    spg_status s = SPG_OK;
+    if (G > 0) {
+        for (int64_t g = 0; g <= G; g++) hb[g] = g * p->nheavy / G;
+        int64_t *hb_d = (int64_t *)ws_alloc(p, sizeof(int64_t) * (size_t)(G + 1));
+        if (!hb_d) s = SPG_OUT_OF_MEMORY;
+        if (!s) s = cuda_check(cudaMemcpyAsync(hb_d, hb.data(), sizeof(int64_t) * (size_t)(G + 1),
+                                               cudaMemcpyHostToDevice, st), "groups");
+        if (!s) {
+            launch(p, k_group_bounds, 1, 64, 0, (const int64_t *)hb_d, G, p->nheavy,
+                   (const int32_t *)(p->binlist + p->bin_off[kBinHeavy]), (const int64_t *)L.it_first, n, bnd);
+            s = cuda_check(cudaMemcpyAsync(p->h_pinned + 24, bnd, sizeof(int64_t) * 2 * (size_t)(G + 1),
+                                           cudaMemcpyDeviceToHost, st), "groups");
+        }
+        if (!s) s = cuda_check(cudaStreamSynchronize(st), "groups");
+        for (int64_t g = 0; g <= G && !s; g++) {
+            ib[g] = p->h_pinned[24 + 2 * g];
+            cb[g] = p->h_pinned[24 + 2 * g + 1];
+        }
+    } else {
+        cb[0] = 0;
+        cb[1] = n;
+    }
+    if (!s) s = cuda_check(cudaMemsetAsync(carry, 0, sizeof(int64_t), st), "memset");
+    if (!s) s = cuda_check(cudaMemsetAsync(broken, 0, sizeof(int), st), "memset");
+    if (!s) s = cuda_check(cudaMemsetAsync(p->d_cnt + kCntNnzCHeavySlot, 0, sizeof(int64_t), st), "memset");
+    if (!s) s = p->acc_f64 ? (p->out_idx64 ? learned_light<double, long long>(p, L) : learned_light<double, int>(p, L))
+                           : (p->out_idx64 ? learned_light<long long, long long>(p, L)
+                                           : learned_light<long long, int>(p, L));
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (!s) s = cuda_check(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking), "stream");
+    if (!s) s = cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    if (!s && G > 0) group_begin(p, kKNumHeavy);
+    const int64_t ngroups = G > 0 ? G : 1;
+    for (int64_t g = 0; g < ngroups && !s; g++) {
+        if (G > 0)
+            s = p->acc_f64 ? (p->out_idx64 ? learned_fused<double, long long>(p, L, ib[g], ib[g + 1])
+                                           : learned_fused<double, int>(p, L, ib[g], ib[g + 1]))
+                           : (p->out_idx64 ? learned_fused<long long, long long>(p, L, ib[g], ib[g + 1])
+                                           : learned_fused<long long, int>(p, L, ib[g], ib[g + 1]));
+        if (!s) s = cuda_check(cudaEventRecord(ev, st), "event");
+        if (!s) s = cuda_check(cudaStreamWaitEvent(side, ev, 0), "event");
+        const int64_t h0 = G > 0 ? hb[g] : 0, h1 = G > 0 ? hb[g + 1] : 0;
+        const int64_t i0 = G > 0 ? ib[g] : 0, i1 = G > 0 ? ib[g + 1] : 0;
+        if (!s)
+            s = p->acc_f64
+                    ? (p->out_idx64 ? learned_place_group<double, long long>(p, L, side, (int)g, cb[g], cb[g + 1], h0, h1,
+                                                                             i0, i1, local, carry, broken, &Copt)
+                                    : learned_place_group<double, int>(p, L, side, (int)g, cb[g], cb[g + 1], h0, h1,
+                                                                       i0, i1, local, carry, broken, &Copt))
+                    : (p->out_idx64 ? learned_place_group<long long, long long>(p, L, side, (int)g, cb[g], cb[g + 1],
+                                                                                h0, h1, i0, i1, local, carry, broken,
+                                                                                &Copt)
+                                    : learned_place_group<long long, int>(p, L, side, (int)g, cb[g], cb[g + 1], h0,
+                                                                          h1, i0, i1, local, carry, broken, &Copt));
+    }
+    if (!s && G > 0) group_end(p, kKNumHeavy);
+    // join the side stream (also after an error, before anything is freed)
+    if (side) {
+        if (ev && cudaEventRecord(ev, side) == cudaSuccess) cudaStreamWaitEvent(st, ev, 0);
+        cudaStreamSynchronize(side);
+        cudaStreamDestroy(side);
+    }
+    if (ev) cudaEventDestroy(ev);
+    if (s) {
+        free_opt();
+        return s;
+    }
+    LTRY(cuda_check(cudaMemcpyAsync(p->h_pinned + 18, L.nflag, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "nflag"));
+    LTRY(cuda_check(cudaMemcpyAsync(p->h_pinned + 20, carry + ngroups, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+                    "nnz"));
+    LTRY(cuda_check(cudaMemcpyAsync(p->h_pinned + 21, p->d_cnt + kCntNnzCHeavySlot, sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, st), "nnz"));
+    LTRY(cuda_check(cudaStreamSynchronize(st), "nflag"));
+    const int64_t nf = p->h_pinned[18];
+    *nrecomputed = nf;
+    if (nf == 0) {
+        // every column was placed: C is the pipelined one (its arrays hold
+        // the predicted capacity, of which the first nnz(C) entries are used)
+        p->nnzC = p->h_pinned[20];
+        p->stats.nnzC = p->nnzC;
+        p->stats.nnzC_heavy = p->h_pinned[21];
+        s = cuda_check(cudaMemcpyAsync(cp_opt, p->Ccolptr, cp_bytes, cudaMemcpyDeviceToDevice, st), "colptr");
+        cudaEventRecord(p->ev[5], st);
+        if (!s) s = read_dev_err(p, "learned");
+        if (s) {
+            free_opt();
+            return s;
+        }
+        spg_csc out{};
+        out.nrows = p->m;
+        out.ncols = n;
+        out.nnz = p->nnzC;
+        out.ptr_type = SPG_IDX_I64;
+        out.idx_type = p->out_idx64 ? SPG_IDX_I64 : SPG_IDX_I32;
+        out.val_type = p->acc_f64 ? SPG_VAL_F64 : SPG_VAL_I64;
+        out.colptr = cp_opt;
+        out.rowidx = ri_opt;
+        out.vals = va_opt;
+        *C = out;
+        return SPG_OK;
+    }
+    free_opt();
     LTRY(cuda_check(cudaMemsetAsync(p->d_cnt + kCntNnzCHeavySlot, 0, sizeof(int64_t), st), "memset"));
     if (n > 0)
         launch(p, k_learned_nnz, grid_for(n, 256, sm * 8), 256, 0, n, p->bin_of, (const unsigned long long *)L.colfill,
                (const int64_t *)L.nnz_light, (const int32_t *)L.flag, L.nnz,
                (unsigned long long *)(p->d_cnt + kCntNnzCHeavySlot));
-    LTRY(cuda_check(cudaMemcpyAsync(p->h_pinned + 18, L.nflag, sizeof(int64_t), cudaMemcpyDeviceToHost, st), "nflag"));
-    LTRY(cuda_check(cudaStreamSynchronize(st), "nflag"));
-    const int64_t nf = p->h_pinned[18];
-    *nrecomputed = nf;
 
     // 4. recompute the overflowed columns through the exact path
     int32_t *flist = nullptr;
