@@ -2,6 +2,8 @@
 // heavy symbolic and numeric kernels).
 #pragma once
 
+#include <type_traits>
+
 #include "spg_internal.cuh"
 
 namespace spg {
@@ -129,7 +131,11 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
                     baseB = sb.start[s + 1] - nB;
                     if (NEED_VAL) bvB = sb.bv[s + 1];
                 }
-                for (int f = f0; f < f1; f += 32 * U) {
+                // one step: U windows located and loaded, then used; FULL: all
+                // 32 x U products lie in the warp's range (every step but the
+                // last), so no lane needs a bounds check
+                auto step = [&](const int f, auto full) {
+                    constexpr bool FULL = decltype(full)::value;
                     int r[U];
                     Acc a[U], bu[U];
                     bool ok[U];
@@ -149,10 +155,10 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
                         const int fi = fb + lane;
                         const bool inB = fi >= nB;
                         const long long e = (inB ? baseB : baseA) + fi;
-                        ok[u] = fi < f1;
+                        bu[u] = inB ? bvB : bvA;
+                        ok[u] = FULL || fi < f1;
                         r[u] = 0;
                         a[u] = Acc(0);
-                        bu[u] = inB ? bvB : bvA;
                         if (ok[u]) {
                             r[u] = __ldg(At_row + e);
                             if (NEED_VAL) a[u] = __ldg(At_val + e);
@@ -161,7 +167,10 @@ __device__ __forceinline__ void cta_products(int64_t p0, int64_t p1, CtaBatch<Ac
 #pragma unroll
                     for (int u = 0; u < U; u++)
                         if (ok[u]) body(r[u], NEED_VAL ? mul_acc<Acc>(a[u], bu[u]) : Acc(0));
-                }
+                };
+                int f = f0;
+                for (; f + 32 * U <= f1; f += 32 * U) step(f, std::true_type{});
+                if (f < f1) step(f, std::false_type{});
             }
         }
         // short segments: products [f0, f1) of this warp, one per lane
