@@ -945,7 +945,8 @@ static spg_status learned_place_group(spg_plan *p, LearnedState &L, cudaStream_t
         p->st = keep;
         if (s) return s;
     } else {
-        cuda_check(cudaMemsetAsync(local, 0, sizeof(int64_t), side), "memset");
+        const spg_status s = cuda_check(cudaMemsetAsync(local, 0, sizeof(int64_t), side), "memset");
+        if (s) return s;
     }
     launch_on(p, side, k_add_carry, grid_for(len + 1, 256, sm * 8), 256, (const int64_t *)local, len,
               (const int64_t *)(carry + g), carry + g + 1, p->Ccolptr + c0);
