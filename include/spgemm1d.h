@@ -462,6 +462,10 @@ spg_status spgemm_outer_multiply(const spg_csc *A, const spg_csc *B, const spg_o
  * A's idx_type, values double or int64; NULL from it gives SPG_OUT_OF_MEMORY),
  * then each group's numeric pass runs on opt->stream while the previous
  * group's part of C is copied to the host on a stream of the call's own.
+ * When C's row and value arrays are page-locked memory that the GPU
+ * addresses through the same pointers (spgemm_host_writable), the numeric
+ * kernels store C into them directly instead (over the CPU-GPU link, no
+ * device copy of C, no copy engine).
  * Device workspace and device copies come from opt->alloc / opt->free (or
  * cudaMallocAsync) and are released before returning; opt->mask, if set,
  * applies as in spgemm_plan (its columns are C's columns).  Blocks until C is
@@ -475,6 +479,11 @@ spg_status spgemm_outer_multiply(const spg_csc *A, const spg_csc *B, const spg_o
  * spgemm_numeric.
  */
 typedef void *(*spg_host_alloc_fn)(size_t bytes, void *ctx);
+/* 1 if kernels can store into the host range [ptr, ptr + bytes) through ptr
+ * itself: page-locked memory (cudaHostRegister or cudaMallocHost) on a
+ * device with cudaDevAttrCanUseHostPointerForRegisteredMem; 0 otherwise
+ * (pageable memory, NULL, bytes = 0). */
+int32_t spgemm_host_writable(const void *ptr, size_t bytes);
 typedef void (*spg_host_free_fn)(void *ptr, size_t bytes, void *ctx);
 spg_status spgemm_1d_multiply_host(const spg_csc *A, const spg_csc *B, const spg_options *opt, int32_t chunks,
                                    spg_host_alloc_fn host_alloc, spg_host_free_fn host_free, void *host_ctx,

@@ -459,15 +459,28 @@ class HostCSC:
         return sum(t.numel() * t.element_size() for t in (self.colptr, self.rowidx, self.vals))
 
 
+def spgemm_host_writable(t: torch.Tensor) -> bool:
+    """True when the library's kernels can store into the CPU tensor t's
+    memory directly (page-locked memory the GPU addresses with the same
+    pointer)."""
+    lib = load_library()
+    lib.spgemm_host_writable.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    lib.spgemm_host_writable.restype = ctypes.c_int32
+    return bool(lib.spgemm_host_writable(t.data_ptr(), t.numel() * t.element_size()))
+
+
 def spgemm_1d_multiply_host(A, B, P=1, b=1024, chunks=4, stream=None, validate=True, light_max=0, slab_rows=0,
-                            split=0, pool: HostPool | None = None, mask=None, mask_complement=False) -> HostCSC:
+                            split=0, pool: HostPool | None = None, mask=None, mask_complement=False,
+                            pinned: bool = True) -> HostCSC:
     """C = A * B for host matrices (objects with nrows, ncols and colptr /
     rowidx / vals as CPU tensors or numpy arrays; pinned memory for full copy
     speed) through spgemm_1d_multiply_host: the copies to and from the GPU
     happen inside the call, C's part of one group of column blocks streaming
     back while the next group computes.  C's arrays come from `pool` when
     given (its earlier contents are overwritten), else from fresh pinned
-    tensors.  mask: an optional output mask on the GPU (as for spgemm_plan)."""
+    tensors (pageable ones with pinned=False: C then always comes back through
+    the copy engine).  mask: an optional output mask on the GPU (as for
+    spgemm_plan)."""
     lib = load_library()
     lib.spgemm_1d_multiply_host.argtypes = [ctypes.POINTER(spg_csc), ctypes.POINTER(spg_csc),
                                             ctypes.POINTER(spg_options), ctypes.c_int32, HOST_ALLOC_FN,
@@ -482,7 +495,7 @@ def spgemm_1d_multiply_host(A, B, P=1, b=1024, chunks=4, stream=None, validate=T
     held = {}
 
     def host_alloc(nbytes, ctx):
-        t = pool.take(nbytes) if pool is not None else torch.empty(int(nbytes), dtype=torch.uint8, pin_memory=True)
+        t = pool.take(nbytes) if pool is not None else torch.empty(int(nbytes), dtype=torch.uint8, pin_memory=pinned)
         if t is None:
             return None
         held[t.data_ptr()] = t

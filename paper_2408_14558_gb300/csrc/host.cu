@@ -88,6 +88,29 @@ spg_status to_device(HostRun &run, const spg_csc &H, spg_csc *D, cudaStream_t st
 // A device-to-host copy issued in pieces: the small read-backs of the later
 // groups' passes queue on the same copy engine and wait for at most one piece
 // instead of the whole transfer.
+// True when the GPU can store into [p, p + bytes) through the same pointer:
+// page-locked (registered or allocated by CUDA) host memory on a device that
+// uses host pointers for registered memory (Grace and other coherent
+// systems).  Pageable memory is never written by a kernel here.
+bool device_writable_host(const void *p, size_t bytes) {
+    if (!p || bytes == 0) return false;
+    int dev = 0, can = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&can, cudaDevAttrCanUseHostPointerForRegisteredMem, dev) != cudaSuccess || !can) {
+        cudaGetLastError();
+        return false;
+    }
+    for (const char *q : {(const char *)p, (const char *)p + bytes - 1}) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || a.devicePointer != (const void *)q) return false;
+    }
+    return true;
+}
+
 spg_status copy_back(void *dst, const void *src, size_t bytes, cudaStream_t st) {
     constexpr size_t kPiece = (size_t)128 << 20;
     for (size_t o = 0; o < bytes; o += kPiece) {
@@ -243,9 +266,20 @@ extern "C" spg_status spgemm_1d_multiply_host(const spg_csc *A, const spg_csc *B
     // every group's numeric set-up (it reads bin sizes back: done before any
     // copy of C occupies the copy engine) and every group's C first
     for (int g = 0; g < G && !s; g++) s = prepare_numeric(run.plans[g]);
+    // direct: the numeric kernels store C's rows and values straight into the
+    // host arrays (page-locked memory the GPU addresses with the same
+    // pointers), with no device copy of C and no copy engine; otherwise each
+    // group's part of C is computed on the device and copied back behind it
+    const bool direct = total > 0 && device_writable_host(hri, ib * (size_t)total) &&
+                        device_writable_host(hva, 8 * (size_t)total);
     std::vector<spg_csc> Cg(G);
     for (int g = 0; g < G && !s; g++) {
         Cg[g].colptr = run.plans[g]->Ccolptr;
+        if (direct) {
+            Cg[g].rowidx = (char *)hri + ib * (size_t)off[g];
+            Cg[g].vals = (char *)hva + 8 * (size_t)off[g];
+            continue;
+        }
         Cg[g].rowidx = run.dev_alloc(ib * (size_t)nnz[g]);
         Cg[g].vals = run.dev_alloc(8 * (size_t)nnz[g]);
         if (!Cg[g].rowidx || !Cg[g].vals) {
@@ -257,6 +291,7 @@ extern "C" spg_status spgemm_1d_multiply_host(const spg_csc *A, const spg_csc *B
     // only for its own pass, so they run while the later groups compute
     for (int g = 0; g < G && !s; g++) {
         s = spgemm_numeric(run.plans[g], &Cg[g]);
+        if (direct) continue;
         cudaEvent_t ev = nullptr;
         if (!s) s = cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
         if (ev) run.events.push_back(ev);
@@ -271,6 +306,7 @@ extern "C" spg_status spgemm_1d_multiply_host(const spg_csc *A, const spg_csc *B
         if (!s && spgemm_plan_stats(run.plans[g], &t) == SPG_OK) add_stats(S, t);
     }
     if (!s) s = cuda_check(cudaStreamSynchronize(run.copy), "C read-back");
+    if (!s && direct) s = cuda_check(cudaStreamSynchronize(st), "C stores");
     // the groups' own column pointers (small), rebased into C's
     std::vector<int64_t> lcp(n + G);
     for (int64_t g = 0, o = 0; g < G && !s; g++) {
@@ -305,4 +341,8 @@ extern "C" spg_status spgemm_1d_multiply_host(const spg_csc *A, const spg_csc *B
     C->vals = hva;
     remember_multiply_stats(S);
     return SPG_OK;
+}
+
+extern "C" int32_t spgemm_host_writable(const void *ptr, size_t bytes) {
+    return device_writable_host(ptr, bytes) ? 1 : 0;
 }

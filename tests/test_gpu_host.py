@@ -67,3 +67,20 @@ def test_host_multiply_edges_and_mask():
         # each group of columns reads its own columns of the mask
         C = g.spgemm_1d_multiply_host(A, B, P=6, b=16, chunks=3, mask=mask_from_pattern(M), mask_complement=comp)
         assert_host_parity(C, oracle.spgemm_masked(A, B, M, comp), f"masked c={comp}")
+
+
+def test_direct_stores_and_copy_engine_agree():
+    """The same product with C's host arrays page-locked (the kernels store C
+    into them directly where the GPU addresses them with the same pointers)
+    and pageable (C always comes back through the copy engine): both equal
+    the oracle."""
+    A = synth.rmat_symmetric(12, 16, seed=8)
+    ref = oracle.spgemm(A, A)
+    hA = pinned(A)
+    pool = g.HostPool(64 << 20)
+    probe = pool.take(1 << 20)
+    direct = g.spgemm_host_writable(probe)
+    assert not g.spgemm_host_writable(torch.empty(1 << 20, dtype=torch.uint8))   # pageable: never
+    for kw in ({"pool": pool}, {"pinned": False}, {}):
+        C = g.spgemm_1d_multiply_host(hA, hA, P=8, b=256, chunks=3, light_max=128, slab_rows=1024, **kw)
+        assert_host_parity(C, ref, f"host arrays {kw or 'pinned'} (direct stores possible: {direct})")
