@@ -40,7 +40,8 @@ CPU_SAMPLE_COLS = 65536      # columns of C computed by the oracle for the CPU b
 REF_SAMPLE_COLS = 16384      # per step of the reference arm
 FLUSH_BYTES = 256 << 20      # > 2 x the 126 MiB L2
 BYTES_PER_NZ = 12            # int32 row id + 8-byte value
-E2E_CHUNKS = 4               # groups of column blocks in the host-buffer call
+E2E_CHUNKS = 4               # groups of column blocks in the host-buffer call when C is copied back
+E2E_CHUNKS_DIRECT = 1        # ... and when the kernels store C into the host pool (no copy to overlap)
 
 
 def parse_args(argv=None):
@@ -465,13 +466,14 @@ def run_e2e(g, torch, A, Ai, steps, world, products_step, nnzc):
     pool = g.HostPool(8 * (A.ncols + 1) + 12 * int(nnzc) + 4096)
     pin_s = time.perf_counter() - t0
     direct = g.spgemm_host_writable(pool.buf[: min(pool.buf.numel(), 1 << 20)])
+    chunks = E2E_CHUNKS_DIRECT if direct else E2E_CHUNKS
     secs, d2h_total = [], 0
     for s in range(steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         d2h = 0
         for h in hosts:
-            C = g.spgemm_1d_multiply_host(h, h, P=P_BLOCKS, b=FETCH_B, chunks=E2E_CHUNKS, pool=pool)
+            C = g.spgemm_1d_multiply_host(h, h, P=P_BLOCKS, b=FETCH_B, chunks=chunks, pool=pool)
             d2h += C.nbytes
             del C
         torch.cuda.synchronize()
@@ -484,7 +486,7 @@ def run_e2e(g, torch, A, Ai, steps, world, products_step, nnzc):
     return {"value": flop_all / t_all / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h_total, "steps": len(secs), "ms_per_step": 1e3 * t_all,
             "ms_per_step_min_max": [round(1e3 * min(secs), 1), round(1e3 * max(secs), 1)],
-            "api": f"spgemm_1d_multiply_host (host buffers, {E2E_CHUNKS} groups of column blocks)",
+            "api": f"spgemm_1d_multiply_host (host buffers, {chunks} group(s) of column blocks)",
             "c_to_host": ("the numeric kernels store C into the pinned host pool directly" if direct else
                           "each group's C copied back by the copy engine behind the next group's numeric pass"),
             "timing": "wall clock, synchronize on both sides of each step; every byte of C is in pinned host "
