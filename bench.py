@@ -40,8 +40,7 @@ CPU_SAMPLE_COLS = 65536      # columns of C computed by the oracle for the CPU b
 REF_SAMPLE_COLS = 16384      # per step of the reference arm
 FLUSH_BYTES = 256 << 20      # > 2 x the 126 MiB L2
 BYTES_PER_NZ = 12            # int32 row id + 8-byte value
-E2E_CHUNKS = 4               # groups of column blocks in the host-buffer call when C is copied back
-E2E_CHUNKS_DIRECT = 1        # ... and when the kernels store C into the host pool (no copy to overlap)
+E2E_CHUNKS = 4               # groups of column blocks in the host-buffer call
 
 
 def parse_args(argv=None):
@@ -468,7 +467,7 @@ def run_e2e(g, torch, A, Ai, steps, world, products_step, nnzc):
     pool = g.HostPool(8 * (A.ncols + 1) + 12 * int(nnzc) + 4096)
     pin_s = time.perf_counter() - t0
     direct = g.spgemm_host_writable(pool.buf[: min(pool.buf.numel(), 1 << 20)])
-    chunks = E2E_CHUNKS_DIRECT if direct else E2E_CHUNKS
+    chunks = E2E_CHUNKS
     secs, d2h_total = [], 0
     for s in range(steps + 1):
         torch.cuda.synchronize()
