@@ -68,30 +68,37 @@ __global__ void k_deg_hist(const void *Acp, int ap64, int64_t k, unsigned long l
     if (threadIdx.x < 64 && h[threadIdx.x]) atomicAdd(hist + threadIdx.x, (unsigned long long)h[threadIdx.x]);
 }
 
-__global__ void k_hub_index(const void *Acp, int ap64, int64_t k, int64_t T, int32_t *hubidx, int *count) {
+__global__ void k_hub_index(const void *Acp, int ap64, int64_t k, int64_t T, int32_t *hubidx, int *count,
+                            int32_t *hubcol) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < k; c += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = ld_ptr(Acp, ap64, c + 1) - ld_ptr(Acp, ap64, c);
-        hubidx[c] = d >= T ? atomicAdd(count, 1) : -1;
+        int h = -1;
+        if (d >= T) {
+            h = atomicAdd(count, 1);
+            hubcol[h] = (int32_t)c;
+        }
+        hubidx[c] = h;
     }
 }
 
-// Warp per column of A: a hub's rows set their bits (rows outside [0, m) are
-// skipped: validation reports them).
-__global__ void k_hub_bits(const void *Acp, int ap64, const void *Arow, int ai64, int64_t k, int64_t m,
-                           const int32_t *hubidx, int64_t Wa, uint32_t *hubbits) {
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = gw; c < k; c += nw) {
-        const int h = hubidx[c];
-        if (h < 0) continue;
-        const int64_t e0 = ld_ptr(Acp, ap64, c), e1 = ld_ptr(Acp, ap64, c + 1);
-        uint32_t *dst = hubbits + (int64_t)h * Wa;
-        for (int64_t e = e0 + lane; e < e1; e += 32) {
-            const int64_t r = ld_ptr(Arow, ai64, e);
-            if ((uint64_t)r < (uint64_t)m) atomicOr(dst + (r >> 5), 1u << (r & 31));
-        }
+// CTA per hub (column hubcol[h] of A): its Wa words built in shared memory
+// with one atomicOr per entry (rows outside [0, m) are skipped: validation
+// reports them), then stored whole (coalesced).
+__global__ void __launch_bounds__(256)
+    k_hub_bits(const void *Acp, int ap64, const void *Arow, int ai64, int64_t m, const int32_t *hubcol, int64_t Wa,
+               uint32_t *hubbits) {
+    extern __shared__ uint32_t hw[];
+    const int64_t c = hubcol[blockIdx.x];
+    for (int64_t w = threadIdx.x; w < Wa; w += blockDim.x) hw[w] = 0;
+    __syncthreads();
+    const int64_t e0 = ld_ptr(Acp, ap64, c), e1 = ld_ptr(Acp, ap64, c + 1);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int64_t r = ld_ptr(Arow, ai64, e);
+        if ((uint64_t)r < (uint64_t)m && (r >> 5) < Wa) atomicOr(hw + (r >> 5), 1u << (r & 31));
     }
+    __syncthreads();
+    uint32_t *dst = hubbits + (int64_t)blockIdx.x * Wa;
+    for (int64_t w = threadIdx.x; w < Wa; w += blockDim.x) dst[w] = hw[w];
 }
 
 // Hub entries one symbolic item may OR instead of walking (the rest walk).
@@ -279,9 +286,11 @@ static spg_status launch_sym_light(spg_plan *p, const int32_t *list, int64_t cnt
 
 // Hub columns of A for the heavy symbolic pass: the threshold is the smallest
 // power of two >= kHubMinDeg whose hubs' bitmaps fit kHubBytes (one
-// histogram read-back).  No hubs: *hubbits stays NULL.
+// histogram read-back).  No hubs (also when one hub's bitmap, rows / 8
+// bytes, exceeds kHubMaxSmem of shared memory): *hubbits stays NULL.
 constexpr int64_t kHubMinDeg = 1024;
 constexpr size_t kHubBytes = size_t(64) << 20;
+constexpr size_t kHubMaxSmem = size_t(192) << 10;  // bitmap words of one hub (rows / 8 bytes) at most
 
 static spg_status build_hubs(spg_plan *p, int32_t **hubidx, uint4 **hubbits, int64_t *Wa4) {
     *hubidx = nullptr;
@@ -293,6 +302,8 @@ static spg_status build_hubs(spg_plan *p, int32_t **hubidx, uint4 **hubbits, int
     const int ap64 = p->A.ptr_type == SPG_IDX_I64;
     // words of a hub bitmap: every base slab of the heavy items (a multiple of 4)
     const int64_t Wa = (int64_t)p->T * (p->R / 32);
+    // a hub's bitmap is built in one CTA's shared memory
+    if ((size_t)Wa * sizeof(uint32_t) > kHubMaxSmem) return SPG_OK;
     unsigned long long *hist = (unsigned long long *)ws_alloc(p, sizeof(unsigned long long) * 64);
     int *count = (int *)ws_alloc(p, sizeof(int) * 4);
     if (!hist || !count) return SPG_OUT_OF_MEMORY;
@@ -313,15 +324,19 @@ static spg_status build_hubs(spg_plan *p, int32_t **hubidx, uint4 **hubbits, int
     }
     if (nh == 0 || lg >= 32) return SPG_OK;
     int32_t *idx = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)k);
+    int32_t *col = (int32_t *)ws_alloc(p, sizeof(int32_t) * (size_t)nh);
     uint32_t *bits = (uint32_t *)ws_alloc(p, sizeof(uint32_t) * (size_t)(nh * Wa));
-    if (!idx || !bits) return SPG_OUT_OF_MEMORY;
+    if (!idx || !col || !bits) return SPG_OUT_OF_MEMORY;
     s = cuda_check(cudaMemsetAsync(count, 0, sizeof(int), st), "memset");
-    if (!s) s = cuda_check(cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (size_t)(nh * Wa), st), "memset");
     if (s) return s;
     launch(p, k_hub_index, grid_for(k, 256, p->sm_count * 4), 256, 0, p->A.colptr, ap64, k, int64_t(1) << lg, idx,
-           count);
-    launch(p, k_hub_bits, grid_for(k * 32, 256, p->sm_count * 8), 256, 0, p->A.colptr, ap64, p->A.rowidx,
-           p->A.idx_type == SPG_IDX_I64, k, p->m, (const int32_t *)idx, Wa, bits);
+           count, col);
+    const size_t smem = sizeof(uint32_t) * (size_t)Wa;
+    s = cuda_check(cudaFuncSetAttribute(k_hub_bits, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "hub bitmaps");
+    if (s) return s;
+    launch(p, k_hub_bits, (unsigned)nh, 256, smem, p->A.colptr, ap64, p->A.rowidx, p->A.idx_type == SPG_IDX_I64,
+           p->m, (const int32_t *)col, Wa, bits);
     s = cuda_check(cudaGetLastError(), "hub bitmaps");
     if (s) return s;
     *hubidx = idx;
