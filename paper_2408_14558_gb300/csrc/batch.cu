@@ -212,19 +212,23 @@ __global__ void k_batch_persistent(const BatchInst *__restrict__ insts, const Ba
             for (int j = tk.c0; j < tk.c1; j++) {
                 if (heavy_col[colb + j]) continue;  // counted by the heavy kernel
                 const int64_t p0 = ld_ptr(in.Bcp, in.bcp64, j), p1 = ld_ptr(in.Bcp, in.bcp64, j + 1);
-                // the class's largest table: every column's bound min(flops, m)
-                // is <= S_MAX / 2, so it needs no pass of its own (a table
-                // sized from the column's own bound probes more: slower)
-                const int logS = LOGS_MAX;
+                // twice the class's largest table, in the warp's value area
+                // (8 bytes per slot of the numeric table: room for 2 x S_MAX
+                // row ids): every column's bound min(flops, m) is <= S_MAX / 2,
+                // so the load factor stays <= 1/4 (a table sized from the
+                // column's own bound probes more: slower)
+                static_assert(sizeof(Acc) == 2 * sizeof(int), "the value area holds 2 x S_MAX row ids");
+                const int logS = LOGS_MAX + 1;
                 const int S = 1 << logS;
-                for (int s = lane; s < S; s += 32) keys[s] = kEmptyKey;
+                int *skeys = (int *)vals;
+                for (int s = lane; s < S; s += 32) skeys[s] = kEmptyKey;
                 __syncwarp();
                 int cnt = 0;
                 bool full = false;
                 warp_products<false, Acc>(
                     p0, p1, lane, ws, in.Arow, (const Acc *)nullptr, seg, [&](int r, Acc) {
                         bool fresh;
-                        if (hash_insert(keys, logS, r, &fresh) < 0) full = true;
+                        if (hash_insert(skeys, logS, r, &fresh) < 0) full = true;
                         cnt += fresh ? 1 : 0;
                     });
                 cnt = warp_sum_i(cnt);
